@@ -1,0 +1,390 @@
+// Stepping drivers: which passes run, in which order, on which buffers.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "engine.h"
+#include "tables.h"
+
+using namespace pss;
+
+namespace {
+
+template <class Rl> V2<Rl> *B(pss_grid *g, int i) { return static_cast<V2<Rl> *>(g->buf[i]); }
+template <class Rl> const V2<Rl> *C(const void *p) { return static_cast<const V2<Rl> *>(p); }
+
+cudaMemcpyKind kind_in(int where) { return where == PSS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
+cudaMemcpyKind kind_out(int where) { return where == PSS_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
+
+// Upload a per-axis table of n complex values given by f(m) -> (re, im) in FP64.
+// For FP32 the value is split into hi + lo (lo = rounding residual).
+template <class F> int upload_hilo(pss_grid *g, int64_t n, F f, void **hi, void **lo)
+{
+    if (g->p.precision == PSS_FP32) {
+        std::vector<float> h(2 * n), l(2 * n);
+        for (int64_t m = 0; m < n; ++m) {
+            double re, im;
+            f(m, &re, &im);
+            h[2 * m] = float(re);
+            h[2 * m + 1] = float(im);
+            l[2 * m] = float(re - double(h[2 * m]));
+            l[2 * m + 1] = float(im - double(h[2 * m + 1]));
+        }
+        int rc = g->upload(hi, h.data(), h.size() * 4);
+        return rc ? rc : g->upload(lo, l.data(), l.size() * 4);
+    }
+    std::vector<double> h(2 * n), l(2 * n, 0.0);
+    for (int64_t m = 0; m < n; ++m) f(m, &h[2 * m], &h[2 * m + 1]);
+    int rc = g->upload(hi, h.data(), h.size() * 8);
+    return rc ? rc : g->upload(lo, l.data(), l.size() * 8);
+}
+
+int upload_twiddles(pss_grid *g, int64_t n, void **dst)
+{
+    if (g->p.precision == PSS_FP32) {
+        auto t = twiddles_f32(n);
+        return g->upload(dst, t.data(), t.size() * 4);
+    }
+    auto t = twiddles_f64(n);
+    return g->upload(dst, t.data(), t.size() * 8);
+}
+
+template <class Rl> int upload_real(pss_grid *g, const std::vector<double> &v, void **dst)
+{
+    std::vector<Rl> r(v.begin(), v.end());
+    return g->upload(dst, r.data(), r.size() * sizeof(Rl));
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+
+int pss_grid::init()
+{
+    nx = p.nx;
+    ny = p.ny;
+    batch = p.batch;
+    npts = nx * ny;
+    ntot = npts * batch;
+    esz = p.precision == PSS_FP32 ? 8 : 16;
+    int rc;
+    if ((rc = cuda(cudaGetDevice(&dev), "cudaGetDevice"))) return rc;
+    if (p.stream) {
+        stream = static_cast<cudaStream_t>(p.stream);
+    } else {
+        if ((rc = cuda(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking), "stream"))) return rc;
+        own_stream = true;
+    }
+    // work arrays
+    nbuf = p.eq == PSS_EQ_NLS ? 3 : p.eq == PSS_EQ_SG ? 5 : 7;
+    for (int i = 0; i < nbuf; ++i)
+        if ((rc = alloc(&buf[i], field_bytes()))) return rc;
+    // tables
+    if ((rc = upload_twiddles(this, nx, &twx))) return rc;
+    if ((rc = upload_twiddles(this, ny, &twy))) return rc;
+    std::vector<double> kx2v(nx), ky2v(ny), kxov(nx), kyov(ny), kpx(nx), kpy(ny);
+    for (int64_t m = 0; m < nx; ++m) {
+        const double k = wavenumber(m, nx, p.lx);
+        kx2v[m] = k * k;
+        kxov[m] = (m == nx / 2) ? 0.0 : k;
+        kpx[m] = (3 * std::llabs(m < nx / 2 ? m : m - nx) < nx) ? 1.0 : 0.0;
+    }
+    for (int64_t m = 0; m < ny; ++m) {
+        const double k = wavenumber(m, ny, p.ly);
+        ky2v[m] = k * k;
+        kyov[m] = (m == ny / 2) ? 0.0 : k;
+        kpy[m] = (3 * std::llabs(m < ny / 2 ? m : m - ny) < ny) ? 1.0 : 0.0;
+    }
+    if ((rc = upload((void **)&kx2d, kx2v.data(), nx * 8))) return rc;
+    if ((rc = upload((void **)&ky2d, ky2v.data(), ny * 8))) return rc;
+    if (p.precision == PSS_FP32) {
+        if ((rc = upload_real<float>(this, kx2v, &kx2)) || (rc = upload_real<float>(this, ky2v, &ky2)) ||
+            (rc = upload_real<float>(this, kxov, &kxo)) || (rc = upload_real<float>(this, kyov, &kyo)) ||
+            (rc = upload_real<float>(this, kpx, &keepx)) || (rc = upload_real<float>(this, kpy, &keepy)))
+            return rc;
+    } else {
+        if ((rc = upload_real<double>(this, kx2v, &kx2)) || (rc = upload_real<double>(this, ky2v, &ky2)) ||
+            (rc = upload_real<double>(this, kxov, &kxo)) || (rc = upload_real<double>(this, kyov, &kyo)) ||
+            (rc = upload_real<double>(this, kpx, &keepx)) || (rc = upload_real<double>(this, kpy, &keepy)))
+            return rc;
+    }
+    if (p.eq == PSS_EQ_NLS) {
+        // exp(-i k^2 tau) per axis, tau = dt/2 (index 0) and dt (index 1)
+        for (int h = 0; h < 2; ++h) {
+            const double tau = h == 0 ? 0.5 * p.dt : p.dt;
+            auto fx = [&](int64_t m, double *re, double *im) {
+                const double ph = kx2v[m] * tau;
+                *re = std::cos(ph);
+                *im = -std::sin(ph);
+            };
+            auto fy = [&](int64_t m, double *re, double *im) {
+                const double ph = ky2v[m] * tau;
+                *re = std::cos(ph);
+                *im = -std::sin(ph);
+            };
+            if ((rc = upload_hilo(this, nx, fx, &ax_hi[h], &ax_lo[h]))) return rc;
+            if ((rc = upload_hilo(this, ny, fy, &by_hi[h], &by_lo[h]))) return rc;
+        }
+    }
+    // reductions
+    const size_t parts = size_t(batch) * 3 * std::max<int64_t>(RED_BLOCKS, nx);
+    if ((rc = alloc((void **)&partials, parts * 8))) return rc;
+    if ((rc = alloc((void **)&sums, size_t(batch) * 3 * 8))) return rc;
+    if ((rc = alloc((void **)&flags, 64))) return rc;
+    if ((rc = cuda(cudaMemset(flags, 0, 64), "memset"))) return rc;
+    void *hp = nullptr;
+    if ((rc = cuda(cudaMallocHost(&hp, size_t(batch) * 3 * 8 + 64), "cudaMallocHost"))) return rc;
+    owned_host.push_back(hp);
+    host_sums = static_cast<double *>(hp);
+    host_flags = reinterpret_cast<unsigned *>(static_cast<char *>(hp) + size_t(batch) * 3 * 8);
+    return cuda(cudaDeviceSynchronize(), "init sync");
+}
+
+int pss_grid::sync()
+{
+    int rc = cuda(cudaStreamSynchronize(stream), "stream sync");
+    if (rc) return rc;
+    if (nonconv_pending) {
+        nonconv_pending = false;
+        return fail(PSS_E_NOT_CONVERGED, "NS fixed point reached max_iter=%d", p.max_iter);
+    }
+    return PSS_OK;
+}
+
+int pss_grid::ns_update_count(int64_t *n)
+{
+    *n = 0;
+    return PSS_OK;
+}
+
+// ----------------------------------------------------------------------------
+// NLS: state buf[0] = row transform of psi (unnormalised); buf[1], buf[2] scratch.
+
+namespace {
+
+template <class Rl> int nls_set(pss_grid *g, const void *a, int where)
+{
+    int rc = g->cuda(cudaMemcpyAsync(g->buf[0], a, g->field_bytes(), kind_in(where), g->stream), "set_state copy");
+    if (rc) return rc;
+    rc = g->cuda(fft_rows<Rl>(B<Rl>(g, 0), g->nx, g->batch * g->ny, -1, Rl(1), C<Rl>(g->twx), g->stream),
+                 "set_state row fft");
+    if (rc) return rc;
+    if (where == PSS_HOST) return g->cuda(cudaStreamSynchronize(g->stream), "set_state sync");
+    return PSS_OK;
+}
+
+template <class Rl> int nls_step(pss_grid *g, int64_t n)
+{
+    const Rl s_mid = Rl(1.0 / (double(g->nx) * double(g->ny)));  // exact: powers of two
+    const Rl s_end = Rl(1.0 / double(g->ny));
+    const Rl sdt = Rl(g->p.sigma * g->p.dt);
+    auto col = [&](int full, Rl scale) {
+        return nls_col_pass<Rl>(B<Rl>(g, 0), g->nx, g->ny, g->batch, scale, C<Rl>(g->ax_hi[full]),
+                                C<Rl>(g->ax_lo[full]), C<Rl>(g->by_hi[full]), C<Rl>(g->by_lo[full]),
+                                C<Rl>(g->twy), g->stream);
+    };
+    if (n == 0) return PSS_OK;
+    cudaError_t e = col(0, s_mid);
+    for (int64_t i = 0; i < n && e == cudaSuccess; ++i) {
+        e = nls_row_pass<Rl>(B<Rl>(g, 0), g->nx, g->batch * g->ny, sdt, C<Rl>(g->twx), g->stream);
+        if (e != cudaSuccess) break;
+        const bool last = (i + 1 == n);
+        e = col(last ? 0 : 1, last ? s_end : s_mid);
+    }
+    return g->cuda(e, "nls step");
+}
+
+// psi (physical) into buf[1]
+template <class Rl> int nls_physical(pss_grid *g)
+{
+    int rc = g->cuda(cudaMemcpyAsync(g->buf[1], g->buf[0], g->field_bytes(), cudaMemcpyDeviceToDevice, g->stream),
+                     "copy");
+    if (rc) return rc;
+    return g->cuda(fft_rows<Rl>(B<Rl>(g, 1), g->nx, g->batch * g->ny, +1, Rl(1.0 / double(g->nx)),
+                                C<Rl>(g->twx), g->stream),
+                   "row inverse");
+}
+
+template <class Rl> int nls_get(pss_grid *g, void *a, int where)
+{
+    int rc = nls_physical<Rl>(g);
+    if (rc) return rc;
+    rc = g->cuda(cudaMemcpyAsync(a, g->buf[1], g->field_bytes(), kind_out(where), g->stream), "get_state copy");
+    if (rc) return rc;
+    return g->sync();
+}
+
+template <class Rl> int nls_conserved(pss_grid *g, double *out)
+{
+    int rc = nls_physical<Rl>(g);
+    if (rc) return rc;
+    rc = g->cuda(cudaMemcpyAsync(g->buf[2], g->buf[0], g->field_bytes(), cudaMemcpyDeviceToDevice, g->stream),
+                 "copy");
+    if (rc) return rc;
+    rc = g->cuda(fft_cols<Rl>(B<Rl>(g, 2), g->nx, g->ny, g->batch, -1, Rl(1), C<Rl>(g->twy), g->stream),
+                 "col fft");
+    if (rc) return rc;
+    rc = g->cuda(nls_sums<Rl>(B<Rl>(g, 1), B<Rl>(g, 2), g->nx, g->ny, g->batch, g->kx2d, g->ky2d, g->partials,
+                              g->sums, g->stream),
+                 "nls sums");
+    if (rc) return rc;
+    rc = g->cuda(cudaMemcpyAsync(g->host_sums, g->sums, size_t(g->batch) * 3 * 8, cudaMemcpyDeviceToHost, g->stream),
+                 "sums copy");
+    if (rc) return rc;
+    if ((rc = g->sync())) return rc;
+    const double dA = g->dA(), inv_n = 1.0 / (double(g->nx) * double(g->ny));
+    bool finite = true;
+    for (int64_t f = 0; f < g->batch; ++f) {
+        const double *s = g->host_sums + 3 * f;
+        out[2 * f] = dA * s[0];
+        out[2 * f + 1] = dA * (0.5 * s[2] * inv_n + 0.25 * g->p.sigma * s[1]);
+        finite = finite && std::isfinite(out[2 * f]) && std::isfinite(out[2 * f + 1]);
+    }
+    return finite ? PSS_OK : g->fail(PSS_E_NONFINITE, "non-finite NLS invariant");
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// dispatch by equation and precision
+
+int pss_grid::set_state(const void *a, const void *b, int where)
+{
+    (void)b;
+    steps = 0;
+    nonconv_pending = false;
+    int rc;
+    if (p.eq == PSS_EQ_NLS) rc = p.precision == PSS_FP32 ? nls_set<float>(this, a, where) : nls_set<double>(this, a, where);
+    else return fail(PSS_E_ARG, "equation %d not available", p.eq);
+    if (!rc) has_state = true;
+    return rc;
+}
+
+int pss_grid::step_n(int64_t n)
+{
+    if (n == 0) return PSS_OK;
+    int rc;
+    if (p.eq == PSS_EQ_NLS) rc = p.precision == PSS_FP32 ? nls_step<float>(this, n) : nls_step<double>(this, n);
+    else return fail(PSS_E_ARG, "equation %d not available", p.eq);
+    if (!rc) steps += n;
+    return rc;
+}
+
+int pss_grid::get_state(void *a, void *b, int where)
+{
+    (void)b;
+    if (p.eq == PSS_EQ_NLS) return p.precision == PSS_FP32 ? nls_get<float>(this, a, where) : nls_get<double>(this, a, where);
+    return fail(PSS_E_ARG, "equation %d not available", p.eq);
+}
+
+int pss_grid::conserved(double *out)
+{
+    if (p.eq == PSS_EQ_NLS) return p.precision == PSS_FP32 ? nls_conserved<float>(this, out) : nls_conserved<double>(this, out);
+    return fail(PSS_E_ARG, "equation %d not available", p.eq);
+}
+
+size_t pss_grid::checkpoint_bytes() const
+{
+    const int nstate = p.eq == PSS_EQ_SG ? 2 : 1;
+    return size_t(nstate) * size_t(ntot) * esz + 16;
+}
+
+int pss_grid::checkpoint(void *buf, int where, bool save)
+{
+    const int nstate = p.eq == PSS_EQ_SG ? 2 : 1;
+    char *b = static_cast<char *>(buf);
+    int rc;
+    for (int i = 0; i < nstate; ++i) {
+        if (save) rc = cuda(cudaMemcpyAsync(b + i * field_bytes(), this->buf[i], field_bytes(), kind_out(where), stream), "checkpoint");
+        else rc = cuda(cudaMemcpyAsync(this->buf[i], b + i * field_bytes(), field_bytes(), kind_in(where), stream), "checkpoint");
+        if (rc) return rc;
+    }
+    int64_t meta[2] = {steps, 0};
+    char *mb = b + nstate * field_bytes();
+    if (save) rc = cuda(cudaMemcpyAsync(mb, meta, 16, where == PSS_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice, stream), "checkpoint meta");
+    else rc = cuda(cudaMemcpyAsync(meta, mb, 16, where == PSS_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost, stream), "checkpoint meta");
+    if (rc) return rc;
+    if ((rc = cuda(cudaStreamSynchronize(stream), "checkpoint sync"))) return rc;
+    if (!save) {
+        steps = meta[0];
+        has_state = true;
+    }
+    return PSS_OK;
+}
+
+// ----------------------------------------------------------------------------
+// standalone 2D transform
+
+namespace {
+std::mutex g_tw_mutex;
+std::map<std::tuple<int, int, int64_t>, void *> g_tw_cache;  // (device, precision, n)
+
+void *cached_twiddles(int dev, int precision, int64_t n, int *rc)
+{
+    std::lock_guard<std::mutex> lk(g_tw_mutex);
+    auto key = std::make_tuple(dev, precision, n);
+    auto it = g_tw_cache.find(key);
+    if (it != g_tw_cache.end()) return it->second;
+    void *d = nullptr;
+    size_t bytes;
+    std::vector<float> tf;
+    std::vector<double> td;
+    const void *src;
+    if (precision == PSS_FP32) {
+        tf = twiddles_f32(n);
+        src = tf.data();
+        bytes = tf.size() * 4;
+    } else {
+        td = twiddles_f64(n);
+        src = td.data();
+        bytes = td.size() * 8;
+    }
+    if (cudaMalloc(&d, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *rc = PSS_E_OOM;
+        return nullptr;
+    }
+    if (cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        *rc = PSS_E_CUDA;
+        return nullptr;
+    }
+    g_tw_cache[key] = d;
+    return d;
+}
+}  // namespace
+
+extern "C" int pss_fft2d(void *data, int64_t nx, int64_t ny, int64_t batch, int precision, int direction,
+                         void *stream)
+{
+    if (!data || batch < 1 || batch > 65535 || (direction != 1 && direction != -1) ||
+        (precision != PSS_FP32 && precision != PSS_FP64))
+        return PSS_E_ARG;
+    auto ok = [](int64_t n) { return n >= 16 && n <= 8192 && (n & (n - 1)) == 0; };
+    if (!ok(nx) || !ok(ny)) return PSS_E_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PSS_E_CUDA;
+    int rc = PSS_OK;
+    void *twx = cached_twiddles(dev, precision, nx, &rc);
+    if (!twx) return rc;
+    void *twy = cached_twiddles(dev, precision, ny, &rc);
+    if (!twy) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    const double inv = direction > 0 ? 1.0 / (double(nx) * double(ny)) : 1.0;
+    if (precision == PSS_FP32) {
+        e = fft_rows<float>(static_cast<float2 *>(data), nx, batch * ny, direction, 1.0f, static_cast<float2 *>(twx), s);
+        if (e == cudaSuccess)
+            e = fft_cols<float>(static_cast<float2 *>(data), nx, ny, batch, direction, float(inv), static_cast<float2 *>(twy), s);
+    } else {
+        e = fft_rows<double>(static_cast<double2 *>(data), nx, batch * ny, direction, 1.0, static_cast<double2 *>(twx), s);
+        if (e == cudaSuccess)
+            e = fft_cols<double>(static_cast<double2 *>(data), nx, ny, batch, direction, inv, static_cast<double2 *>(twy), s);
+    }
+    return e == cudaSuccess ? PSS_OK : PSS_E_CUDA;
+}

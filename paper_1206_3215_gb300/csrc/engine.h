@@ -1,0 +1,69 @@
+// The grid handle behind the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pss.h"
+#include "internal.h"
+
+struct pss_grid {
+    pss_params p{};
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t nx = 0, ny = 0, batch = 0, npts = 0, ntot = 0;
+    size_t esz = 0;  // bytes of one complex element
+    std::string err;
+
+    std::vector<void *> owned;       // cudaMalloc'd, freed by pss_destroy
+    std::vector<void *> owned_host;  // cudaMallocHost'd
+
+    // complex work arrays, ntot elements each (meaning depends on eq)
+    void *buf[8] = {};
+    int nbuf = 0;
+
+    // tables (device)
+    void *twx = nullptr, *twy = nullptr;                           // twiddles, precision
+    void *ax_hi[2] = {}, *ax_lo[2] = {}, *by_hi[2] = {}, *by_lo[2] = {};  // NLS [half, full]
+    double *kx2d = nullptr, *ky2d = nullptr;                       // |k|^2 per axis, FP64
+    void *kx2 = nullptr, *ky2 = nullptr;                           // |k|^2 per axis, precision
+    void *kxo = nullptr, *kyo = nullptr;                           // odd-derivative k, precision
+    void *keepx = nullptr, *keepy = nullptr;                       // NS dealias mask (0/1), precision
+
+    // reductions
+    double *partials = nullptr;  // batch * RED_BLOCKS * 3 (and NS per-tile partials)
+    double *sums = nullptr;      // batch * 3
+    double *host_sums = nullptr; // pinned, batch * 3
+    unsigned *flags = nullptr;   // device status bits
+    unsigned *host_flags = nullptr;
+
+    // NS fixed-point bookkeeping (device, per field)
+    void *ns_field = nullptr;
+    int *host_active = nullptr;
+
+    int64_t steps = 0;
+    bool has_state = false;
+    bool nonconv_pending = false;
+
+    int fail(int code, const char *fmt, ...);
+    int alloc(void **p, size_t bytes);
+    int upload(void **p, const void *host, size_t bytes);
+    int cuda(cudaError_t e, const char *what);
+
+    int init();
+    int set_state(const void *a, const void *b, int where);
+    int step_n(int64_t n);
+    int get_state(void *a, void *b, int where);
+    int conserved(double *out);
+    int sync();
+    int ns_update_count(int64_t *n);
+    size_t checkpoint_bytes() const;
+    int checkpoint(void *buf, int where, bool save);
+    void release_extra() {}
+
+    size_t field_bytes() const { return size_t(ntot) * esz; }
+    double dA() const { return (p.lx / double(nx)) * (p.ly / double(ny)); }
+};

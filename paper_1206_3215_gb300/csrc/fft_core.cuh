@@ -1,0 +1,202 @@
+// Stockham FFT building blocks for sm_103a.
+//
+// A length-N transform is carried by T = N/P threads that each hold P points in
+// registers.  Stage s has radix R_s (P, or a smaller power of two for the last
+// stage) and span Ns = R_0 ... R_{s-1}; butterfly j (0 <= j < N/R) reads
+// elements j + r N/R, multiplies element r by W_{Ns R}^{(j mod Ns) r}, takes an
+// R-point DFT in registers and writes output r to (j div Ns) Ns R + (j mod Ns)
+// + r Ns (the self-sorting Stockham order).  Thread t owns butterflies
+// j = t + q T, so its register m always holds element t + T m: the first stage
+// reads, and the last stage writes, unit-stride runs across threads, which is
+// what makes the global loads and stores of the row and column passes
+// coalesced.  Between stages the points are exchanged through shared memory.
+//
+// Twiddles W_N^e = exp(-2 pi i e / N) come from a table computed in FP64 on
+// the host and rounded once; the small-radix constants are exact decimal
+// expansions rounded once by the compiler.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace pss {
+
+template <class V> __device__ __forceinline__ V cadd(V a, V b) { return {a.x + b.x, a.y + b.y}; }
+template <class V> __device__ __forceinline__ V csub(V a, V b) { return {a.x - b.x, a.y - b.y}; }
+template <class V> __device__ __forceinline__ V cmul(V a, V b)
+{
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <class V> __device__ __forceinline__ V cmulc(V a, V b)
+{
+    return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <class V, class R> __device__ __forceinline__ V cscale(V a, R s) { return {a.x * s, a.y * s}; }
+
+// multiply by exp(DIR * i * pi / 2) = DIR * i
+template <int DIR, class V> __device__ __forceinline__ V mul_i(V a)
+{
+    if (DIR > 0) return {-a.y, a.x};
+    return {a.y, -a.x};
+}
+
+// cos(pi j / 16), j = 0..8
+__host__ __device__ constexpr double cos_pi16(int j)
+{
+    return j == 0 ? 1.0
+         : j == 1 ? 0.98078528040323044912618223613424
+         : j == 2 ? 0.92387953251128675612818318939679
+         : j == 3 ? 0.83146961230254523707878837761791
+         : j == 4 ? 0.70710678118654752440084436210485
+         : j == 5 ? 0.55557023301960222474283081394853
+         : j == 6 ? 0.38268343236508977172845998403040
+         : j == 7 ? 0.19509032201612826784828486847702
+                  : 0.0;
+}
+// cos and sin of 2 pi m / 32 for 0 <= m < 16
+__host__ __device__ constexpr double cos32(int m) { return m <= 8 ? cos_pi16(m) : -cos_pi16(16 - m); }
+__host__ __device__ constexpr double sin32(int m) { return m <= 8 ? cos_pi16(8 - m) : cos_pi16(m - 8); }
+
+// z * exp(DIR * 2 pi i k / RAD), 0 <= k < RAD/2, RAD | 32
+template <int RAD, int DIR, int K, class V> __device__ __forceinline__ V rot(V z)
+{
+    using R = decltype(z.x);
+    constexpr int m = K * (32 / RAD);
+    if constexpr (m == 0) {
+        return z;
+    } else if constexpr (m == 8) {
+        return mul_i<DIR>(z);
+    } else if constexpr (m == 4 || m == 12) {
+        // (cos, DIR sin) with |cos| = sin = 1/sqrt(2)
+        constexpr R h = R(0.70710678118654752440084436210485);
+        constexpr R c = (m == 4) ? h : -h;
+        constexpr R s = DIR > 0 ? h : -h;
+        return {c * z.x - s * z.y, c * z.y + s * z.x};
+    } else {
+        constexpr R c = R(cos32(m));
+        constexpr R s = R(DIR > 0 ? sin32(m) : -sin32(m));
+        return {c * z.x - s * z.y, c * z.y + s * z.x};
+    }
+}
+
+template <int RAD, int DIR, int S, int K, class V> __device__ __forceinline__ void dif_level(V *v)
+{
+    if constexpr (K < RAD / 2) {
+        V a = v[K * S], b = v[(K + RAD / 2) * S];
+        v[K * S] = cadd(a, b);
+        v[(K + RAD / 2) * S] = rot<RAD, DIR, K>(csub(a, b));
+        dif_level<RAD, DIR, S, K + 1>(v);
+    }
+}
+
+// In-register DFT of RAD points v[0], v[S], ..., v[(RAD-1) S] by radix-2
+// decimation in frequency; the result is left in bit-reversed order.
+template <int RAD, int DIR, int S, class V> __device__ __forceinline__ void dft_dif(V *v)
+{
+    if constexpr (RAD > 1) {
+        dif_level<RAD, DIR, S, 0>(v);
+        dft_dif<RAD / 2, DIR, S>(v);
+        dft_dif<RAD / 2, DIR, S>(v + (RAD / 2) * S);
+    }
+}
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+__host__ __device__ constexpr int bitrev(int r, int bits)
+{
+    return bits == 0 ? 0 : ((r & 1) << (bits - 1)) | bitrev(r >> 1, bits - 1);
+}
+
+// Stage list of a length-N transform with P points per thread.
+template <int N, int P> struct Plan {
+    static_assert((N & (N - 1)) == 0 && (P & (P - 1)) == 0 && P <= N && P <= 32, "bad plan");
+    static constexpr int T = N / P;
+    static constexpr int LOGN = ilog2(N), LOGP = ilog2(P);
+    static constexpr int FULL = LOGN / LOGP, REM = LOGN % LOGP;
+    static constexpr int STAGES = FULL + (REM ? 1 : 0);
+    __host__ __device__ static constexpr int radix(int s) { return s < FULL ? P : (1 << REM); }
+    __host__ __device__ static constexpr int span(int s) { return s == 0 ? 1 : span(s - 1) * radix(s - 1); }
+};
+
+// Shared-memory view of one transform's N points with one pad slot every
+// 2^PADLOG points (breaks the power-of-two strides of the Stockham writes).
+template <class V, int PADLOG> struct SmemLine {
+    V *base;
+    __host__ __device__ static constexpr int padded(int n) { return n + (n >> PADLOG); }
+    __device__ __forceinline__ V &operator[](int i) const { return base[i + (i >> PADLOG)]; }
+};
+
+template <bool BLOCK> __device__ __forceinline__ void fft_sync()
+{
+    if constexpr (BLOCK) __syncthreads();
+    else __syncwarp();
+}
+
+// One Stockham stage s of a length-N transform (DIR = -1 forward, +1 inverse).
+// On entry register m holds element t + T m of the stage input; on exit (for
+// the last stage) register m holds output element t + T m.  Other stages leave
+// their output in shared memory and reload the next stage's input.
+template <int N, int P, int DIR, int S, bool BLOCK, class V, class Sm>
+__device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const V *__restrict__ tw)
+{
+    using PL = Plan<N, P>;
+    constexpr int R = PL::radix(S), NS = PL::span(S), T = PL::T, Q = P / R;
+    constexpr bool LAST = (S == PL::STAGES - 1);
+    if constexpr (S > 0) {
+        // twiddles W_{NS R}^{(j mod NS) r} = W_N^{(j mod NS) r N/(NS R)}
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int jm = (t + q * T) & (NS - 1);
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const V w = __ldg(tw + jm * r * (N / (NS * R)));
+                v[q + r * Q] = DIR < 0 ? cmul(v[q + r * Q], w) : cmulc(v[q + r * Q], w);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) dft_dif<R, DIR, Q>(v + q);
+    constexpr int BITS = ilog2(R);
+    if constexpr (LAST) {
+        // undo the bit reversal: output r of butterfly q sits in v[q + bitrev(r) Q]
+        V o[P];
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int r = 0; r < R; ++r) o[q + r * Q] = v[q + bitrev(r, BITS) * Q];
+#pragma unroll
+        for (int m = 0; m < P; ++m) v[m] = o[m];
+    } else {
+        fft_sync<BLOCK>();  // previous readers of shared memory are done
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int j = t + q * T;
+            const int base = (j / NS) * NS * R + (j & (NS - 1));
+#pragma unroll
+            for (int r = 0; r < R; ++r) sm[base + r * NS] = v[q + bitrev(r, BITS) * Q];
+        }
+        fft_sync<BLOCK>();
+#pragma unroll
+        for (int m = 0; m < P; ++m) v[m] = sm[t + T * m];
+    }
+}
+
+template <int N, int P, int DIR, int S, bool BLOCK, class V, class Sm>
+__device__ __forceinline__ void fft_stages(V (&v)[P], const Sm &sm, int t, const V *__restrict__ tw)
+{
+    if constexpr (S < Plan<N, P>::STAGES) {
+        fft_stage<N, P, DIR, S, BLOCK>(v, sm, t, tw);
+        fft_stages<N, P, DIR, S + 1, BLOCK>(v, sm, t, tw);
+    }
+}
+
+// Full unnormalised length-N transform of the points held by the T threads
+// t = 0..T-1 (register m = element t + T m, in and out).
+template <int N, int P, int DIR, bool BLOCK, class V, class Sm>
+__device__ __forceinline__ void block_fft(V (&v)[P], const Sm &sm, int t, const V *__restrict__ tw)
+{
+    fft_stages<N, P, DIR, 0, BLOCK>(v, sm, t, tw);
+}
+
+}  // namespace pss

@@ -1,0 +1,85 @@
+// Dispatch from a run-time grid length to the compiled kernel shapes.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+
+#include "passes.cuh"
+
+namespace pss {
+
+// Supported lengths of either grid axis.
+#define PSS_FOR_EACH_N(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
+
+// Opt a kernel into more than 48 KB of dynamic shared memory, once per
+// device (attributes belong to the device's context).  done_mask is a static
+// of the caller, one per kernel instance.
+template <class K>
+inline cudaError_t allow_smem(K kernel, size_t bytes, std::atomic<unsigned> &done_mask)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned bit = 1u << (dev & 31);
+    if (done_mask.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e == cudaSuccess) done_mask.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
+template <class Rl, int N, class Op>
+inline cudaError_t launch_row_n(Op op, const V2<Rl> *tw, int64_t rows_total, cudaStream_t s)
+{
+    using C = RowCfg<Rl, N>;
+    auto k = k_row<Rl, N, Op>;
+    static std::atomic<unsigned> done{0};
+    cudaError_t e = allow_smem(k, C::SMEM, done);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (rows_total + C::ROWS - 1) / C::ROWS;
+    if (blocks <= 0) return cudaSuccess;
+    k<<<dim3(unsigned(blocks)), C::THREADS, C::SMEM, s>>>(op, tw, rows_total);
+    return cudaGetLastError();
+}
+
+template <class Rl, int N, class Op>
+inline cudaError_t launch_col_n(Op op, const V2<Rl> *tw, int64_t nx, int64_t batch, cudaStream_t s)
+{
+    using C = ColCfg<Rl, N>;
+    auto k = k_col<Rl, N, Op>;
+    static std::atomic<unsigned> done{0};
+    cudaError_t e = allow_smem(k, C::SMEM, done);
+    if (e != cudaSuccess) return e;
+    if (batch <= 0) return cudaSuccess;
+    k<<<dim3(unsigned(nx / C::W), unsigned(batch)), C::THREADS, C::SMEM, s>>>(op, tw);
+    return cudaGetLastError();
+}
+
+// Row pass over every row of a [batch][ny][nx] array: transform length nx.
+template <class Rl, class Op>
+inline cudaError_t launch_row(int64_t nx, Op op, const V2<Rl> *tw, int64_t rows_total, cudaStream_t s)
+{
+    switch (nx) {
+#define PSS_CASE(N) \
+    case N: return launch_row_n<Rl, N>(op, tw, rows_total, s);
+        PSS_FOR_EACH_N(PSS_CASE)
+#undef PSS_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Column pass over every column of a [batch][ny][nx] array: transform length ny.
+template <class Rl, class Op>
+inline cudaError_t launch_col(int64_t ny, int64_t nx, Op op, const V2<Rl> *tw, int64_t batch,
+                              cudaStream_t s)
+{
+    switch (ny) {
+#define PSS_CASE(N) \
+    case N: return launch_col_n<Rl, N>(op, tw, nx, batch, s);
+        PSS_FOR_EACH_N(PSS_CASE)
+#undef PSS_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pss

@@ -18,3 +18,22 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def lib():
+    """The CUDA library, built in place if needed (compiles on a CPU-only box too)."""
+    from paper_1206_3215_gb300 import build as _b  # noqa: F401
+    import paper_1206_3215_gb300.build as B
+    B.build()
+    import paper_1206_3215_gb300 as P
+    P.load_library()
+    return P
+
+
+@pytest.fixture(scope="session")
+def cuda_device(lib):
+    import torch
+    assert torch.cuda.is_available(), "GPU test needs a CUDA device"
+    torch.cuda.init()
+    return torch.device("cuda:0")

@@ -1,0 +1,154 @@
+"""Parity of the NLS split-step path (Eq. 1, Section 4.1) through the C ABI
+against the FP64 oracle, closed forms and invariants (Eq. 2)."""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as S
+from gpu_util import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+L = 20 * math.pi
+# tolerances: FP64 path vs oracle (double rounding only), and the FP32 targets
+# (relative L2 error of the state and relative mass drift)
+TOL64 = 1e-10
+TOL32_STATE = 1e-5
+TOL32_MASS = 1e-6
+
+
+def _grid(lib, n, precision, batch=1, **kw):
+    return lib.Grid("nls", n, precision, batch=batch, lx=L, ly=L, x0=-L / 2, y0=-L / 2, **kw)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_config1_64_matches_oracle(lib, orc, cuda_device, precision):
+    n, dt, steps = 64, 1e-3, 200
+    p0 = S.nls_gaussian(n)
+    ref = orc.nls_run(p0, L, L, dt, steps, merged=False)
+    g = _grid(lib, n, precision, dt=dt)
+    g.set_state(p0[None])
+    g.step(steps)
+    got = g.get_state()[0]
+    err = rel_l2(got, ref)
+    assert err <= (TOL64 if precision == "fp64" else TOL32_STATE), err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_plane_wave_1024_closed_form(lib, cuda_device, precision):
+    n, dt, steps, A = 1024, 1e-3, 2000, 0.5
+    p0 = S.nls_plane_wave(n, A=A, m=(3, 2))
+    g = _grid(lib, n, precision, dt=dt)
+    g.set_state(p0[None])
+    m0 = g.conserved()[0, 0]
+    g.step(steps)
+    got = g.get_state()[0]
+    k2 = (2 * math.pi / L) ** 2 * 13
+    exact = p0 * np.exp(-1j * (k2 + A * A) * dt * steps)
+    err = rel_l2(got, exact)
+    assert err <= (1e-11 if precision == "fp64" else TOL32_STATE), err
+    m1, e1 = g.conserved()[0]
+    assert abs(m1 - A * A * L * L) / (A * A * L * L) <= (1e-13 if precision == "fp64" else TOL32_MASS)
+    assert abs(m1 - m0) / m0 <= (1e-13 if precision == "fp64" else TOL32_MASS)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_config2_1024_matches_oracle_and_conserves_mass(lib, orc, cuda_device, precision):
+    # 1024^2, dt = 1e-3; the oracle runs the merged Strang sequence in FP64
+    n, dt, steps = 1024, 1e-3, 2000
+    p0 = S.nls_gaussian(n, seed=S.SEED_BASE + 1)
+    ref = orc.nls_run(p0, L, L, dt, steps, merged=True)
+    g = _grid(lib, n, precision, dt=dt)
+    g.set_state(p0[None])
+    (m0, e0), = g.conserved()
+    g.step(steps)
+    got = g.get_state()[0]
+    (m1, e1), = g.conserved()
+    rm, re_ = orc.nls_invariants(ref, L, L)
+    err = rel_l2(got, ref)
+    if precision == "fp64":
+        assert err <= TOL64, err
+        assert abs(m1 - rm) / rm <= 1e-12 and abs(e1 - re_) / abs(re_) <= 1e-9
+    else:
+        assert err <= TOL32_STATE, err
+        assert abs(m1 - m0) / m0 <= TOL32_MASS, (m1 - m0) / m0
+
+
+def test_batch_fields_are_independent_and_bitwise_equal_alone(lib, cuda_device):
+    n, dt, steps = 128, 1e-3, 50
+    fields = S.nls_gaussian(n, batch=3)
+    g = _grid(lib, n, "fp32", batch=3, dt=dt)
+    g.set_state(fields)
+    g.step(steps)
+    together = g.get_state()
+    for b in range(3):
+        g1 = _grid(lib, n, "fp32", dt=dt)
+        g1.set_state(fields[b:b + 1])
+        g1.step(steps)
+        assert np.array_equal(g1.get_state()[0], together[b])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_checkpoint_resume_is_bitwise(lib, cuda_device, precision):
+    n, dt = 256, 1e-3
+    p0 = S.nls_gaussian(n)[None]
+    a = _grid(lib, n, precision, dt=dt)
+    a.set_state(p0)
+    a.step(30)
+    ck = a.checkpoint()
+    a.step(20)
+    b = _grid(lib, n, precision, dt=dt)
+    b.restore(ck)
+    b.step(20)
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert b.stats()[0] == 50
+
+
+def test_split_calls_equal_one_call(lib, cuda_device):
+    n, dt = 64, 1e-3
+    p0 = S.nls_gaussian(n)[None]
+    a = _grid(lib, n, "fp64", dt=dt)
+    a.set_state(p0)
+    a.step(40)
+    b = _grid(lib, n, "fp64", dt=dt)
+    b.set_state(p0)
+    b.step(15)
+    b.step(0)
+    b.step(25)
+    assert rel_l2(b.get_state(), a.get_state()) <= 1e-13
+
+
+def test_non_square_grid_matches_oracle(lib, orc, cuda_device):
+    nx, ny, dt, steps = 128, 32, 1e-3, 50
+    lx, ly = 20 * math.pi, 5 * math.pi
+    rng = np.random.default_rng(7)
+    p0 = rng.standard_normal((ny, nx)) * 0.3 + 1j * rng.standard_normal((ny, nx)) * 0.3
+    ref = orc.nls_run(p0, lx, ly, dt, steps, sigma=-1.0)
+    g = lib.Grid("nls", (nx, ny), "fp64", lx=lx, ly=ly, dt=dt, sigma=-1.0)
+    g.set_state(p0[None])
+    g.step(steps)
+    assert rel_l2(g.get_state()[0], ref) <= TOL64
+
+
+def test_invariants_match_oracle(lib, orc, cuda_device):
+    n = 256
+    p0 = S.nls_gaussian(n)
+    g = _grid(lib, n, "fp64")
+    g.set_state(p0[None])
+    (m, e), = g.conserved()
+    rm, re_ = orc.nls_invariants(p0, L, L)
+    assert abs(m - rm) <= 1e-13 * rm and abs(e - re_) <= 1e-12 * abs(re_)
+
+
+def test_errors_leave_handle_usable(lib, cuda_device):
+    g = _grid(lib, 64, "fp32")
+    with pytest.raises(lib.PssError) as e:
+        g.step(1)
+    assert e.value.code == lib.PSS_E_STATE
+    with pytest.raises(lib.PssError) as e:
+        lib.pss_step_n(g.h, -1)
+    assert e.value.code == lib.PSS_E_ARG
+    g.set_state(S.nls_gaussian(64)[None])
+    g.step(2)
+    assert np.isfinite(g.get_state()).all()
