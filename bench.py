@@ -1,0 +1,383 @@
+"""Throughput benchmark: 2D cubic NLS split-step Fourier (arXiv:1206.3215,
+Section 4.1) on one GB300, in grid-point-steps per second.
+
+Workload: NLS i psi_t + Lap psi = |psi|^2 psi on [-10 pi, 10 pi)^2, 1024 x 1024
+points, dt = 1e-3, psi0 = exp(-(x^2+y^2)) + 1e-3 complex Gaussian noise, FP32
+(complex64) state.  A batch of independent fields (seeded per field) is
+advanced together so that the resident state (batch * 8 MiB) is larger than
+the 129 MB L2: every pass streams from HBM.  One bench step = one Strang time
+step of every field of the batch.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this build
+has) on the host cores, on a bounded sample of the same workload.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "2D NLS split-step Gpt-steps/s FP32 vs FP64 at <=1e-6 mass drift; served p99 latency"
+UNIT = "Gpt-steps/s"
+N = 1024
+L = 20 * math.pi
+DT = 1e-3
+E2E_STEPS = 2000  # one full solve of the 1024^2 configuration per e2e iteration
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1206_3215_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary, only if
+    the kernel sources are unchanged since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(kernel)
+        if e and e.get("source_hash") == kernel_source_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(seconds_target: float = 12.0):
+    """The FP64 oracle as it stands, on one 1024^2 field, merged Strang steps."""
+    import numpy as np  # noqa: F401
+    import oracle
+    import synthetic as S
+    p0 = S.nls_gaussian(N, seed=S.SEED_BASE + 1)
+    t0 = time.perf_counter()
+    oracle.nls_run(p0, L, L, DT, 2, merged=True)
+    per = (time.perf_counter() - t0) / 2
+    steps = max(2, min(400, int(seconds_target / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.nls_run(p0, L, L, DT, steps, merged=True)
+    dt = time.perf_counter() - t0
+    return {"value": N * N * steps / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"1 field of {N}x{N}, {steps} merged Strang steps, FP64 C oracle (OpenMP)"}
+
+
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import synthetic as S
+    p0 = S.nls_gaussian(args.n, seed=S.SEED_BASE + 1)
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.nls_run(p0, L, L, DT, 1, merged=True)
+    t0 = time.perf_counter()
+    oracle.nls_run(p0, L, L, DT, args.steps, merged=True)
+    dt = time.perf_counter() - t0
+    v = args.n * args.n * args.steps / dt / 1e9
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"NLS {args.n}x{args.n} split-step, 1 field per step, FP64 CPU oracle",
+                   "n": args.n, "dt": DT, "box": "[-10pi,10pi)^2"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"1 field of {args.n}x{args.n}, {args.steps} steps"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1206_3215_gb300 as P
+    import synthetic as S
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n, B = args.n, args.batch
+
+    # per-rank fields (replicas: independent problems per GPU)
+    fields = S.nls_gaussian(n, seed=S.SEED_BASE + 1 + 100000 * rank, batch=B).astype(np.complex64)
+    psi0 = torch.from_numpy(fields).to(dev)
+
+    g = P.Grid("nls", n, "fp32", batch=B, lx=L, ly=L, x0=-L / 2, y0=-L / 2, dt=DT,
+               stream=stream.cuda_stream)
+    g.set_state(psi0)
+    mass0 = g.conserved()[:, 0].copy()
+
+    # warm-up
+    g.step(args.warmup)
+    g.sync()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # timed region: K steps through the library, device-resident state
+    P.pss_set_profiling(g.h, True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    prof = P.pss_profile_read(g.h)
+    P.pss_set_profiling(g.h, False)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    mass1 = g.conserved()[:, 0]
+    total_steps = args.warmup + args.steps
+    drift = float(np.max(np.abs(mass1 - mass0) / mass0))
+
+    value = world * B * n * n * args.steps / (ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel (row or column pass): algorithmic bytes =
+    # one read + one write of the complex64 state per pass
+    hbm, peak_kind = peaks()
+    bytes_per_pass = 2 * B * n * n * 8
+    rows_n, rows_ms = prof["row"]
+    cols_n, cols_ms = prof["col"]
+    dom = "col" if cols_ms >= rows_ms else "row"
+    dn, dms = (cols_n, cols_ms) if dom == "col" else (rows_n, rows_ms)
+    achieved = bytes_per_pass / (dms / dn / 1e3) / 1e9 if dn else None
+    kernel_name = {"col": "k_col<float, 1024, NlsCol<float>>", "row": "k_row<float, 1024, NlsRow<float>>"}[dom]
+    traffic = ncu_traffic(kernel_name)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                "kernel": kernel_name, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": bytes_per_pass,
+                "pass_ms": {"row": rows_ms / max(rows_n, 1), "col": cols_ms / max(cols_n, 1)},
+                # whole step (row + column pass) against the same peak
+                "step_frac": 2 * bytes_per_pass / (ms / args.steps / 1e3) / 1e9 / hbm}
+
+    # FP64 path on the same workload (fewer steps; it is ALU bound on GB300)
+    fp64 = None
+    if not args.no_fp64:
+        g64 = P.Grid("nls", n, "fp64", batch=B, lx=L, ly=L, dt=DT, stream=stream.cuda_stream)
+        g64.set_state(torch.from_numpy(fields.astype(np.complex128)).to(dev))
+        g64.step(2)
+        g64.sync()
+        k64 = max(4, args.steps // 10)
+        torch.cuda.synchronize(dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        g64.step(k64)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = f0.elapsed_time(f1)
+        fp64 = {"value": world * B * n * n * k64 / (ms64 / 1e3) / 1e9, "unit": UNIT, "steps": k64,
+                "ms_per_step": ms64 / k64}
+        g64.close()
+
+    # end to end through the public API with host buffers: one full solve of
+    # E2E_STEPS steps per iteration (upload psi0, step, read back psi and mass)
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(fields).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        ge = P.Grid("nls", n, "fp32", batch=B, lx=L, ly=L, dt=DT, stream=stream.cuda_stream)
+        cq = np.zeros(2 * B)
+
+        def solve():
+            P.pss_set_state(ge.h, host_in.data_ptr(), None, P.PSS_HOST)
+            P.pss_step_n(ge.h, E2E_STEPS)
+            cq[:] = P.pss_conserved_quantities(ge.h, cap=2 * B)
+            P.pss_get_state(ge.h, host_out.data_ptr(), None, P.PSS_HOST)
+
+        solve()  # warm-up
+        iters = 2
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            solve()
+        torch.cuda.synchronize(dev)
+        te = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([te], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        nbytes = B * n * n * 8
+        drift2000 = float(np.max(np.abs(cq[0::2] - mass0) / mass0))
+        e2e = {"value": world * B * n * n * E2E_STEPS * iters / te / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes / E2E_STEPS, "d2h_bytes_per_step": (nbytes + 16 * B) / E2E_STEPS,
+               "per_solve": {"steps": E2E_STEPS, "h2d_bytes": nbytes, "d2h_bytes": nbytes + 16 * B,
+                             "seconds": te / iters, "mass_drift_max_rel": drift2000}}
+        ge.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        try:
+            cpu = cpu_baseline()
+        except Exception as ex:  # the GPU number stands without it
+            cpu = {"error": str(ex)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32)", "data": "synthetic",
+            "config": {"workload": f"NLS {n}x{n} Strang split-step, batch {B} fields per GPU, FP32",
+                       "n": n, "batch_per_gpu": B, "dt": DT, "box": "[-10pi,10pi)^2",
+                       "state_bytes_per_gpu": B * n * n * 8,
+                       "l2": "inputs larger than L2 (state > 129 MB, streamed every pass)",
+                       "parallelism": f"replicas x{world}"},
+            "accuracy": {"mass_drift_max_rel": drift, "steps_run": total_steps},
+            "fp64": fp64,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": prof["launches"],
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    g.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

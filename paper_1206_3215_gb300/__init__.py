@@ -26,7 +26,7 @@ EXPORTED = [
     "pss_default_params", "pss_create_grid", "pss_set_state", "pss_step_n", "pss_get_state",
     "pss_conserved_quantities", "pss_stats", "pss_checkpoint_size", "pss_checkpoint_save",
     "pss_checkpoint_load", "pss_sync", "pss_destroy", "pss_last_error", "pss_fft2d",
-    "pss_version",
+    "pss_version", "pss_set_profiling", "pss_profile_read",
 ]
 
 
@@ -80,6 +80,8 @@ def load_library(path: str = LIB_PATH):
             "pss_last_error": (ctypes.c_char_p, [P]),
             "pss_fft2d": (I, [P, I64, I64, I64, I, I, P]),
             "pss_version": (ctypes.c_char_p, []),
+            "pss_set_profiling": (I, [P, I]),
+            "pss_profile_read": (I, [P, P, I, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -167,6 +169,18 @@ def pss_fft2d(ptr: int, nx: int, ny: int, batch: int, precision: int, direction:
     rc = load_library().pss_fft2d(ptr, nx, ny, batch, precision, direction, stream)
     if rc != PSS_OK:
         raise PssError(rc, "pss_fft2d failed")
+
+
+def pss_set_profiling(h, on: bool) -> None:
+    _check(load_library().pss_set_profiling(h, int(on)), h)
+
+
+def pss_profile_read(h) -> dict:
+    out = np.zeros(7, dtype=np.float64)
+    cnt = ctypes.c_int()
+    _check(load_library().pss_profile_read(h, out.ctypes.data, 7, ctypes.byref(cnt)), h)
+    return {"launches": int(out[0]), "row": (int(out[1]), float(out[2])),
+            "col": (int(out[3]), float(out[4])), "other": (int(out[5]), float(out[6]))}
 
 
 def pss_version() -> str:

@@ -224,6 +224,38 @@ int pss_stats(pss_grid *g, int64_t *steps, int64_t *ns_updates)
     return rc;
 }
 
+int pss_set_profiling(pss_grid *g, int on)
+{
+    if (!g) return PSS_E_ARG;
+    DeviceGuard dg(g->dev);
+    int rc = g->profile_resolve();
+    if (rc) return rc;
+    g->profiling = on != 0;
+    for (int k = 0; k < 3; ++k) {
+        g->prof_ms[k] = 0;
+        g->prof_n[k] = 0;
+    }
+    g->launches = 0;
+    return PSS_OK;
+}
+
+int pss_profile_read(pss_grid *g, double *out, int cap, int *count)
+{
+    if (!g) return PSS_E_ARG;
+    if (!out || !count) return g->fail(PSS_E_ARG, "profile_read: null pointer");
+    *count = 7;
+    if (cap < 7) return g->fail(PSS_E_ARG, "profile_read: cap < 7");
+    DeviceGuard dg(g->dev);
+    int rc = g->profile_resolve();
+    if (rc) return rc;
+    out[0] = double(g->launches);
+    for (int k = 0; k < 3; ++k) {
+        out[1 + 2 * k] = double(g->prof_n[k]);
+        out[2 + 2 * k] = g->prof_ms[k];
+    }
+    return PSS_OK;
+}
+
 int pss_sync(pss_grid *g)
 {
     if (!g) return PSS_E_ARG;

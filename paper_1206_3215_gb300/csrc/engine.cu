@@ -17,31 +17,27 @@ namespace {
 
 template <class Rl> V2<Rl> *B(pss_grid *g, int i) { return static_cast<V2<Rl> *>(g->buf[i]); }
 template <class Rl> const V2<Rl> *C(const void *p) { return static_cast<const V2<Rl> *>(p); }
+template <class Rl> const TW<Rl> *Tw(const void *p) { return static_cast<const TW<Rl> *>(p); }
 
 cudaMemcpyKind kind_in(int where) { return where == PSS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
 cudaMemcpyKind kind_out(int where) { return where == PSS_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
 
-// Upload a per-axis table of n complex values given by f(m) -> (re, im) in FP64.
-// For FP32 the value is split into hi + lo (lo = rounding residual).
-template <class F> int upload_hilo(pss_grid *g, int64_t n, F f, void **hi, void **lo)
+// Upload a per-axis table of n complex values given by f(m) -> (re, im) in FP64,
+// in the twiddle layout of the grid's precision (FP32: hi + lo quadruples).
+template <class F> int upload_cplx_table(pss_grid *g, int64_t n, F f, void **dst)
 {
     if (g->p.precision == PSS_FP32) {
-        std::vector<float> h(2 * n), l(2 * n);
+        std::vector<float> t(4 * n);
         for (int64_t m = 0; m < n; ++m) {
             double re, im;
             f(m, &re, &im);
-            h[2 * m] = float(re);
-            h[2 * m + 1] = float(im);
-            l[2 * m] = float(re - double(h[2 * m]));
-            l[2 * m + 1] = float(im - double(h[2 * m + 1]));
+            hilo_f32(re, im, &t[4 * m]);
         }
-        int rc = g->upload(hi, h.data(), h.size() * 4);
-        return rc ? rc : g->upload(lo, l.data(), l.size() * 4);
+        return g->upload(dst, t.data(), t.size() * 4);
     }
-    std::vector<double> h(2 * n), l(2 * n, 0.0);
-    for (int64_t m = 0; m < n; ++m) f(m, &h[2 * m], &h[2 * m + 1]);
-    int rc = g->upload(hi, h.data(), h.size() * 8);
-    return rc ? rc : g->upload(lo, l.data(), l.size() * 8);
+    std::vector<double> t(2 * n);
+    for (int64_t m = 0; m < n; ++m) f(m, &t[2 * m], &t[2 * m + 1]);
+    return g->upload(dst, t.data(), t.size() * 8);
 }
 
 int upload_twiddles(pss_grid *g, int64_t n, void **dst)
@@ -114,21 +110,19 @@ int pss_grid::init()
             return rc;
     }
     if (p.eq == PSS_EQ_NLS) {
-        // exp(-i k^2 tau) per axis, tau = dt/2 (index 0) and dt (index 1)
+        // exp(-i k^2 tau) - 1 = (-2 sin^2(k^2 tau / 2), -sin(k^2 tau)) per axis,
+        // tau = dt/2 (index 0) and dt (index 1); no cancellation for small k
         for (int h = 0; h < 2; ++h) {
             const double tau = h == 0 ? 0.5 * p.dt : p.dt;
-            auto fx = [&](int64_t m, double *re, double *im) {
-                const double ph = kx2v[m] * tau;
-                *re = std::cos(ph);
+            auto km1 = [](double ph, double *re, double *im) {
+                const double sh = std::sin(0.5 * ph);
+                *re = -2.0 * sh * sh;
                 *im = -std::sin(ph);
             };
-            auto fy = [&](int64_t m, double *re, double *im) {
-                const double ph = ky2v[m] * tau;
-                *re = std::cos(ph);
-                *im = -std::sin(ph);
-            };
-            if ((rc = upload_hilo(this, nx, fx, &ax_hi[h], &ax_lo[h]))) return rc;
-            if ((rc = upload_hilo(this, ny, fy, &by_hi[h], &by_lo[h]))) return rc;
+            auto fx = [&](int64_t m, double *re, double *im) { km1(kx2v[m] * tau, re, im); };
+            auto fy = [&](int64_t m, double *re, double *im) { km1(ky2v[m] * tau, re, im); };
+            if ((rc = upload_cplx_table(this, nx, fx, &ax[h]))) return rc;
+            if ((rc = upload_cplx_table(this, ny, fy, &by[h]))) return rc;
         }
     }
     // reductions
@@ -156,6 +150,41 @@ int pss_grid::sync()
     return PSS_OK;
 }
 
+int pss_grid::pass_begin(int kind)
+{
+    ++launches;
+    if (!profiling) return PSS_OK;
+    while (ev_pool.size() < ev_used + 2) {
+        cudaEvent_t e;
+        int rc = cuda(cudaEventCreate(&e), "event create");
+        if (rc) return rc;
+        ev_pool.push_back(e);
+    }
+    ev_kind.push_back(kind);
+    return cuda(cudaEventRecord(ev_pool[ev_used++], stream), "event record");
+}
+
+int pss_grid::pass_end()
+{
+    if (!profiling) return PSS_OK;
+    return cuda(cudaEventRecord(ev_pool[ev_used++], stream), "event record");
+}
+
+int pss_grid::profile_resolve()
+{
+    int rc = cuda(cudaStreamSynchronize(stream), "profile sync");
+    if (rc) return rc;
+    for (size_t i = 0; i < ev_kind.size(); ++i) {
+        float ms = 0.f;
+        if ((rc = cuda(cudaEventElapsedTime(&ms, ev_pool[2 * i], ev_pool[2 * i + 1]), "elapsed"))) return rc;
+        prof_ms[ev_kind[i]] += ms;
+        prof_n[ev_kind[i]] += 1;
+    }
+    ev_kind.clear();
+    ev_used = 0;
+    return PSS_OK;
+}
+
 int pss_grid::ns_update_count(int64_t *n)
 {
     *n = 0;
@@ -171,7 +200,7 @@ template <class Rl> int nls_set(pss_grid *g, const void *a, int where)
 {
     int rc = g->cuda(cudaMemcpyAsync(g->buf[0], a, g->field_bytes(), kind_in(where), g->stream), "set_state copy");
     if (rc) return rc;
-    rc = g->cuda(fft_rows<Rl>(B<Rl>(g, 0), g->nx, g->batch * g->ny, -1, Rl(1), C<Rl>(g->twx), g->stream),
+    rc = g->cuda(fft_rows<Rl>(B<Rl>(g, 0), g->nx, g->batch * g->ny, -1, Rl(1), Tw<Rl>(g->twx), g->stream),
                  "set_state row fft");
     if (rc) return rc;
     if (where == PSS_HOST) return g->cuda(cudaStreamSynchronize(g->stream), "set_state sync");
@@ -184,17 +213,23 @@ template <class Rl> int nls_step(pss_grid *g, int64_t n)
     const Rl s_end = Rl(1.0 / double(g->ny));
     const Rl sdt = Rl(g->p.sigma * g->p.dt);
     auto col = [&](int full, Rl scale) {
-        return nls_col_pass<Rl>(B<Rl>(g, 0), g->nx, g->ny, g->batch, scale, C<Rl>(g->ax_hi[full]),
-                                C<Rl>(g->ax_lo[full]), C<Rl>(g->by_hi[full]), C<Rl>(g->by_lo[full]),
-                                C<Rl>(g->twy), g->stream);
+        return nls_col_pass<Rl>(B<Rl>(g, 0), g->nx, g->ny, g->batch, scale, Tw<Rl>(g->ax[full]),
+                                Tw<Rl>(g->by[full]), Tw<Rl>(g->twy), g->stream);
     };
     if (n == 0) return PSS_OK;
+    int rc;
+    if ((rc = g->pass_begin(1))) return rc;
     cudaError_t e = col(0, s_mid);
+    if ((rc = g->pass_end())) return rc;
     for (int64_t i = 0; i < n && e == cudaSuccess; ++i) {
-        e = nls_row_pass<Rl>(B<Rl>(g, 0), g->nx, g->batch * g->ny, sdt, C<Rl>(g->twx), g->stream);
+        if ((rc = g->pass_begin(0))) return rc;
+        e = nls_row_pass<Rl>(B<Rl>(g, 0), g->nx, g->batch * g->ny, sdt, Tw<Rl>(g->twx), g->stream);
+        if ((rc = g->pass_end())) return rc;
         if (e != cudaSuccess) break;
         const bool last = (i + 1 == n);
+        if ((rc = g->pass_begin(1))) return rc;
         e = col(last ? 0 : 1, last ? s_end : s_mid);
+        if ((rc = g->pass_end())) return rc;
     }
     return g->cuda(e, "nls step");
 }
@@ -206,7 +241,7 @@ template <class Rl> int nls_physical(pss_grid *g)
                      "copy");
     if (rc) return rc;
     return g->cuda(fft_rows<Rl>(B<Rl>(g, 1), g->nx, g->batch * g->ny, +1, Rl(1.0 / double(g->nx)),
-                                C<Rl>(g->twx), g->stream),
+                                Tw<Rl>(g->twx), g->stream),
                    "row inverse");
 }
 
@@ -226,7 +261,7 @@ template <class Rl> int nls_conserved(pss_grid *g, double *out)
     rc = g->cuda(cudaMemcpyAsync(g->buf[2], g->buf[0], g->field_bytes(), cudaMemcpyDeviceToDevice, g->stream),
                  "copy");
     if (rc) return rc;
-    rc = g->cuda(fft_cols<Rl>(B<Rl>(g, 2), g->nx, g->ny, g->batch, -1, Rl(1), C<Rl>(g->twy), g->stream),
+    rc = g->cuda(fft_cols<Rl>(B<Rl>(g, 2), g->nx, g->ny, g->batch, -1, Rl(1), Tw<Rl>(g->twy), g->stream),
                  "col fft");
     if (rc) return rc;
     rc = g->cuda(nls_sums<Rl>(B<Rl>(g, 1), B<Rl>(g, 2), g->nx, g->ny, g->batch, g->kx2d, g->ky2d, g->partials,
@@ -378,9 +413,9 @@ extern "C" int pss_fft2d(void *data, int64_t nx, int64_t ny, int64_t batch, int 
     cudaError_t e;
     const double inv = direction > 0 ? 1.0 / (double(nx) * double(ny)) : 1.0;
     if (precision == PSS_FP32) {
-        e = fft_rows<float>(static_cast<float2 *>(data), nx, batch * ny, direction, 1.0f, static_cast<float2 *>(twx), s);
+        e = fft_rows<float>(static_cast<float2 *>(data), nx, batch * ny, direction, 1.0f, static_cast<float4 *>(twx), s);
         if (e == cudaSuccess)
-            e = fft_cols<float>(static_cast<float2 *>(data), nx, ny, batch, direction, float(inv), static_cast<float2 *>(twy), s);
+            e = fft_cols<float>(static_cast<float2 *>(data), nx, ny, batch, direction, float(inv), static_cast<float4 *>(twy), s);
     } else {
         e = fft_rows<double>(static_cast<double2 *>(data), nx, batch * ny, direction, 1.0, static_cast<double2 *>(twx), s);
         if (e == cudaSuccess)

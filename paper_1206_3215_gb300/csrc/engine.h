@@ -27,7 +27,7 @@ struct pss_grid {
 
     // tables (device)
     void *twx = nullptr, *twy = nullptr;                           // twiddles, precision
-    void *ax_hi[2] = {}, *ax_lo[2] = {}, *by_hi[2] = {}, *by_lo[2] = {};  // NLS [half, full]
+    void *ax[2] = {}, *by[2] = {};  // NLS exp(-i k^2 tau) per axis, [dt/2, dt]
     double *kx2d = nullptr, *ky2d = nullptr;                       // |k|^2 per axis, FP64
     void *kx2 = nullptr, *ky2 = nullptr;                           // |k|^2 per axis, precision
     void *kxo = nullptr, *kyo = nullptr;                           // odd-derivative k, precision
@@ -43,6 +43,18 @@ struct pss_grid {
     // NS fixed-point bookkeeping (device, per field)
     void *ns_field = nullptr;
     int *host_active = nullptr;
+
+    // tracing: event pairs around passes (kind 0 row, 1 column, 2 other)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<int> ev_kind;  // kind of pair i = events 2i, 2i+1
+    double prof_ms[3] = {0, 0, 0};
+    int64_t prof_n[3] = {0, 0, 0};
+    int64_t launches = 0;
+    int pass_begin(int kind);
+    int pass_end();
+    int profile_resolve();
 
     int64_t steps = 0;
     bool has_state = false;
@@ -62,7 +74,11 @@ struct pss_grid {
     int ns_update_count(int64_t *n);
     size_t checkpoint_bytes() const;
     int checkpoint(void *buf, int where, bool save);
-    void release_extra() {}
+    void release_extra()
+    {
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        ev_pool.clear();
+    }
 
     size_t field_bytes() const { return size_t(ntot) * esz; }
     double dA() const { return (p.lx / double(nx)) * (p.ly / double(ny)); }

@@ -12,8 +12,10 @@
 // coalesced.  Between stages the points are exchanged through shared memory.
 //
 // Twiddles W_N^e = exp(-2 pi i e / N) come from a table computed in FP64 on
-// the host and rounded once; the small-radix constants are exact decimal
-// expansions rounded once by the compiler.
+// the host; the small-radix constants are exact decimal expansions.  In FP32
+// every constant is carried as a high and a low part and applied with one
+// rounding (cmul_hl), which removes the systematic gain or loss of |z| that
+// a rounded constant would repeat in every pass of every step.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -59,6 +61,32 @@ __host__ __device__ constexpr double cos_pi16(int j)
 __host__ __device__ constexpr double cos32(int m) { return m <= 8 ? cos_pi16(m) : -cos_pi16(16 - m); }
 __host__ __device__ constexpr double sin32(int m) { return m <= 8 ? cos_pi16(8 - m) : cos_pi16(m - 8); }
 
+// z (hr + lr + i (hi + li)) with one rounding of the exact constant per
+// output component: the small product with the low part is folded in inside
+// the fused multiply-adds, so the rounding error of the stored high part does
+// not bias the result (it would otherwise shrink or grow |z| by the same
+// factor in every pass).
+__device__ __forceinline__ float2 cmul_hl(float2 z, float hr, float hi, float lr, float li)
+{
+    const float cr = __fmaf_rn(z.x, lr, -z.y * li);
+    const float ci = __fmaf_rn(z.x, li, z.y * lr);
+    return {__fmaf_rn(z.x, hr, __fmaf_rn(-z.y, hi, cr)), __fmaf_rn(z.x, hi, __fmaf_rn(z.y, hr, ci))};
+}
+
+// twiddle product z * w (forward) or z * conj(w) (inverse)
+template <int DIR> __device__ __forceinline__ float2 twmul(float2 z, float4 w)
+{
+    if (DIR < 0) return cmul_hl(z, w.x, w.y, w.z, w.w);
+    return cmul_hl(z, w.x, -w.y, w.z, -w.w);
+}
+template <int DIR> __device__ __forceinline__ double2 twmul(double2 z, double2 w)
+{
+    return DIR < 0 ? cmul(z, w) : cmulc(z, w);
+}
+
+// s * x with s = hi + lo held exactly to one rounding
+__device__ __forceinline__ float mul_hl(float x, float h, float l) { return __fmaf_rn(x, h, x * l); }
+
 // z * exp(DIR * 2 pi i k / RAD), 0 <= k < RAD/2, RAD | 32
 template <int RAD, int DIR, int K, class V> __device__ __forceinline__ V rot(V z)
 {
@@ -69,15 +97,26 @@ template <int RAD, int DIR, int K, class V> __device__ __forceinline__ V rot(V z
     } else if constexpr (m == 8) {
         return mul_i<DIR>(z);
     } else if constexpr (m == 4 || m == 12) {
-        // (cos, DIR sin) with |cos| = sin = 1/sqrt(2)
-        constexpr R h = R(0.70710678118654752440084436210485);
-        constexpr R c = (m == 4) ? h : -h;
-        constexpr R s = DIR > 0 ? h : -h;
-        return {c * z.x - s * z.y, c * z.y + s * z.x};
+        // (c, s) = (sc h, ss h) with h = 1/sqrt(2): c x - s y = h (sc x - ss y)
+        constexpr double H = 0.70710678118654752440084436210485;
+        constexpr R sc = (m == 4) ? R(1) : R(-1);
+        constexpr R ss = DIR > 0 ? R(1) : R(-1);
+        const R dr = sc * z.x - ss * z.y, di = sc * z.y + ss * z.x;
+        if constexpr (sizeof(R) == 4) {
+            constexpr float hh = float(H), hl = float(H - double(float(H)));
+            return {mul_hl(dr, hh, hl), mul_hl(di, hh, hl)};
+        } else {
+            return {R(H) * dr, R(H) * di};
+        }
     } else {
-        constexpr R c = R(cos32(m));
-        constexpr R s = R(DIR > 0 ? sin32(m) : -sin32(m));
-        return {c * z.x - s * z.y, c * z.y + s * z.x};
+        constexpr double c = cos32(m), s = DIR > 0 ? sin32(m) : -sin32(m);
+        if constexpr (sizeof(R) == 4) {
+            constexpr float ch = float(c), sh = float(s);
+            constexpr float cl = float(c - double(ch)), sl = float(s - double(sh));
+            return cmul_hl(z, ch, sh, cl, sl);
+        } else {
+            return {R(c) * z.x - R(s) * z.y, R(c) * z.y + R(s) * z.x};
+        }
     }
 }
 
@@ -137,8 +176,8 @@ template <bool BLOCK> __device__ __forceinline__ void fft_sync()
 // On entry register m holds element t + T m of the stage input; on exit (for
 // the last stage) register m holds output element t + T m.  Other stages leave
 // their output in shared memory and reload the next stage's input.
-template <int N, int P, int DIR, int S, bool BLOCK, class V, class Sm>
-__device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const V *__restrict__ tw)
+template <int N, int P, int DIR, int S, bool BLOCK, class V, class Sm, class W>
+__device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const W *__restrict__ tw)
 {
     using PL = Plan<N, P>;
     constexpr int R = PL::radix(S), NS = PL::span(S), T = PL::T, Q = P / R;
@@ -150,8 +189,8 @@ __device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const 
             const int jm = (t + q * T) & (NS - 1);
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                const V w = __ldg(tw + jm * r * (N / (NS * R)));
-                v[q + r * Q] = DIR < 0 ? cmul(v[q + r * Q], w) : cmulc(v[q + r * Q], w);
+                const W w = __ldg(tw + jm * r * (N / (NS * R)));
+                v[q + r * Q] = twmul<DIR>(v[q + r * Q], w);
             }
         }
     }
@@ -182,8 +221,8 @@ __device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const 
     }
 }
 
-template <int N, int P, int DIR, int S, bool BLOCK, class V, class Sm>
-__device__ __forceinline__ void fft_stages(V (&v)[P], const Sm &sm, int t, const V *__restrict__ tw)
+template <int N, int P, int DIR, int S, bool BLOCK, class V, class Sm, class W>
+__device__ __forceinline__ void fft_stages(V (&v)[P], const Sm &sm, int t, const W *__restrict__ tw)
 {
     if constexpr (S < Plan<N, P>::STAGES) {
         fft_stage<N, P, DIR, S, BLOCK>(v, sm, t, tw);
@@ -193,8 +232,8 @@ __device__ __forceinline__ void fft_stages(V (&v)[P], const Sm &sm, int t, const
 
 // Full unnormalised length-N transform of the points held by the T threads
 // t = 0..T-1 (register m = element t + T m, in and out).
-template <int N, int P, int DIR, bool BLOCK, class V, class Sm>
-__device__ __forceinline__ void block_fft(V (&v)[P], const Sm &sm, int t, const V *__restrict__ tw)
+template <int N, int P, int DIR, bool BLOCK, class V, class Sm, class W>
+__device__ __forceinline__ void block_fft(V (&v)[P], const Sm &sm, int t, const W *__restrict__ tw)
 {
     fft_stages<N, P, DIR, 0, BLOCK>(v, sm, t, tw);
 }

@@ -12,26 +12,34 @@ template <> struct vec2<float> { using type = float2; };
 template <> struct vec2<double> { using type = double2; };
 template <class Rl> using V2 = typename vec2<Rl>::type;
 
+// Twiddle table entry: FP32 keeps the FP64 value as hi + lo (float4 =
+// hi.re, hi.im, lo.re, lo.im) so that products are formed with one rounding
+// of the exact constant; FP64 stores the value itself.
+template <class Rl> struct twid;
+template <> struct twid<float> { using type = float4; };
+template <> struct twid<double> { using type = double2; };
+template <class Rl> using TW = typename twid<Rl>::type;
+
 // ---- plain transforms (k_fft.cu) -------------------------------------------
 // dir -1 forward, +1 inverse (unnormalised); the result is multiplied by scale.
 template <class Rl>
 cudaError_t fft_rows(V2<Rl> *data, int64_t nx, int64_t rows_total, int dir, Rl scale,
-                     const V2<Rl> *twx, cudaStream_t s);
+                     const TW<Rl> *twx, cudaStream_t s);
 template <class Rl>
 cudaError_t fft_cols(V2<Rl> *data, int64_t nx, int64_t ny, int64_t batch, int dir, Rl scale,
-                     const V2<Rl> *twy, cudaStream_t s);
+                     const TW<Rl> *twy, cudaStream_t s);
 
 // ---- NLS passes (k_nls.cu) ---------------------------------------------------
 // Row pass: row inverse FFT, psi <- psi exp(-i sigma dt |psi|^2), row forward FFT.
 template <class Rl>
 cudaError_t nls_row_pass(V2<Rl> *data, int64_t nx, int64_t rows_total, Rl sigma_dt,
-                         const V2<Rl> *twx, cudaStream_t s);
+                         const TW<Rl> *twx, cudaStream_t s);
 // Column pass: column forward FFT, multiply by scale * a[x] * b[y]
-// (a = exp(-i kx^2 tau), b = exp(-i ky^2 tau), each as hi + lo), column inverse FFT.
+// (a = exp(-i kx^2 tau), b = exp(-i ky^2 tau); the tables hold a - 1 and
+// b - 1, stored like twiddles), column inverse FFT.
 template <class Rl>
 cudaError_t nls_col_pass(V2<Rl> *data, int64_t nx, int64_t ny, int64_t batch, Rl scale,
-                         const V2<Rl> *ax_hi, const V2<Rl> *ax_lo, const V2<Rl> *by_hi,
-                         const V2<Rl> *by_lo, const V2<Rl> *twy, cudaStream_t s);
+                         const TW<Rl> *ax, const TW<Rl> *by, const TW<Rl> *twy, cudaStream_t s);
 
 // ---- deterministic FP64 reductions (k_reduce.cu) -----------------------------
 constexpr int RED_BLOCKS = 128;  // partial sums per field

@@ -6,7 +6,7 @@ namespace pss {
 
 template <class Rl>
 cudaError_t fft_rows(V2<Rl> *data, int64_t nx, int64_t rows_total, int dir, Rl scale,
-                     const V2<Rl> *twx, cudaStream_t s)
+                     const TW<Rl> *twx, cudaStream_t s)
 {
     if (dir < 0) return launch_row<Rl>(nx, RowFft<Rl, -1>{data, scale}, twx, rows_total, s);
     return launch_row<Rl>(nx, RowFft<Rl, +1>{data, scale}, twx, rows_total, s);
@@ -14,18 +14,18 @@ cudaError_t fft_rows(V2<Rl> *data, int64_t nx, int64_t rows_total, int dir, Rl s
 
 template <class Rl>
 cudaError_t fft_cols(V2<Rl> *data, int64_t nx, int64_t ny, int64_t batch, int dir, Rl scale,
-                     const V2<Rl> *twy, cudaStream_t s)
+                     const TW<Rl> *twy, cudaStream_t s)
 {
     if (dir < 0) return launch_col<Rl>(ny, nx, ColFft<Rl, -1>{data, nx, scale}, twy, batch, s);
     return launch_col<Rl>(ny, nx, ColFft<Rl, +1>{data, nx, scale}, twy, batch, s);
 }
 
-template cudaError_t fft_rows<float>(float2 *, int64_t, int64_t, int, float, const float2 *,
+template cudaError_t fft_rows<float>(float2 *, int64_t, int64_t, int, float, const float4 *,
                                      cudaStream_t);
 template cudaError_t fft_rows<double>(double2 *, int64_t, int64_t, int, double, const double2 *,
                                       cudaStream_t);
 template cudaError_t fft_cols<float>(float2 *, int64_t, int64_t, int64_t, int, float,
-                                     const float2 *, cudaStream_t);
+                                     const float4 *, cudaStream_t);
 template cudaError_t fft_cols<double>(double2 *, int64_t, int64_t, int64_t, int, double,
                                       const double2 *, cudaStream_t);
 

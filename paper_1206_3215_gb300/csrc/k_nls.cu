@@ -19,7 +19,7 @@ template <class Rl> struct NlsRow {
     Rl sigma_dt;
     template <int N, int P, bool BLOCK, class Sm>
     __device__ __forceinline__ void run(int64_t row, bool ok, int t, const Sm &sm,
-                                        const V2<Rl> *tw) const
+                                        const TW<Rl> *tw) const
     {
         constexpr int T = N / P;
         V2<Rl> v[P];
@@ -44,35 +44,37 @@ template <class Rl> struct NlsRow {
     }
 };
 
-// z (h + l) with the low part only for single precision
-template <bool HILO, class V> __device__ __forceinline__ V mul_hl(V z, V h, V l)
+// Propagator exp(-i k^2 tau) applied as z + z (K - 1): K - 1 is tabulated
+// exactly (hi + lo in FP32) and the small increment z (K - 1) is formed with
+// relative accuracy, so each output is one rounding of z + increment.  The
+// direct product z K would round x cos + y sin for the slowly rotating low
+// wavenumbers in the same direction step after step (K is within a few ulp of
+// 1 there), which shows up as a steady drift of the mass in FP32.
+template <class V, class W> __device__ __forceinline__ V apply_km1(V z, W km1)
 {
-    if constexpr (HILO) return cadd(cmul(z, h), cmul(z, l));
-    else return cmul(z, h);
+    return cadd(z, twmul<-1>(z, km1));
 }
 
 template <class Rl> struct NlsCol {
     V2<Rl> *data;
     int64_t nx;
     Rl scale;
-    const V2<Rl> *ax_hi, *ax_lo, *by_hi, *by_lo;
+    const TW<Rl> *ax, *by;  // exp(-i kx^2 tau) - 1, exp(-i ky^2 tau) - 1
     template <int N, int P, bool BLOCK, class Sm>
     __device__ __forceinline__ void run(int64_t field, int x, int t, const Sm &sm,
-                                        const V2<Rl> *tw) const
+                                        const TW<Rl> *tw) const
     {
         constexpr int T = N / P;
-        constexpr bool HILO = sizeof(Rl) == 4;
         V2<Rl> v[P];
         V2<Rl> *p = data + field * N * nx + x;
         load_line<P, T>(v, p, nx, t, true);
         block_fft<N, P, -1, BLOCK>(v, sm, t, tw);
-        const V2<Rl> ah = cscale(__ldg(ax_hi + x), scale);
-        const V2<Rl> al = cscale(__ldg(ax_lo + x), scale);
+        const TW<Rl> a = __ldg(ax + x);
 #pragma unroll
         for (int m = 0; m < P; ++m) {
-            const int y = t + T * m;
-            V2<Rl> z = mul_hl<HILO>(v[m], ah, al);
-            v[m] = mul_hl<HILO>(z, __ldg(by_hi + y), __ldg(by_lo + y));
+            // scale is a power of two: exact
+            const V2<Rl> z = apply_km1(cscale(v[m], scale), a);
+            v[m] = apply_km1(z, __ldg(by + t + T * m));
         }
         block_fft<N, P, +1, BLOCK>(v, sm, t, tw);
         store_line<P, T>(v, p, nx, t, true);
@@ -81,26 +83,24 @@ template <class Rl> struct NlsCol {
 
 template <class Rl>
 cudaError_t nls_row_pass(V2<Rl> *data, int64_t nx, int64_t rows_total, Rl sigma_dt,
-                         const V2<Rl> *twx, cudaStream_t s)
+                         const TW<Rl> *twx, cudaStream_t s)
 {
     return launch_row<Rl>(nx, NlsRow<Rl>{data, sigma_dt}, twx, rows_total, s);
 }
 
 template <class Rl>
 cudaError_t nls_col_pass(V2<Rl> *data, int64_t nx, int64_t ny, int64_t batch, Rl scale,
-                         const V2<Rl> *ax_hi, const V2<Rl> *ax_lo, const V2<Rl> *by_hi,
-                         const V2<Rl> *by_lo, const V2<Rl> *twy, cudaStream_t s)
+                         const TW<Rl> *ax, const TW<Rl> *by, const TW<Rl> *twy, cudaStream_t s)
 {
-    return launch_col<Rl>(ny, nx, NlsCol<Rl>{data, nx, scale, ax_hi, ax_lo, by_hi, by_lo}, twy,
-                          batch, s);
+    return launch_col<Rl>(ny, nx, NlsCol<Rl>{data, nx, scale, ax, by}, twy, batch, s);
 }
 
 #define PSS_INST(Rl)                                                                            \
-    template cudaError_t nls_row_pass<Rl>(V2<Rl> *, int64_t, int64_t, Rl, const V2<Rl> *,        \
+    template cudaError_t nls_row_pass<Rl>(V2<Rl> *, int64_t, int64_t, Rl, const TW<Rl> *,        \
                                           cudaStream_t);                                          \
     template cudaError_t nls_col_pass<Rl>(V2<Rl> *, int64_t, int64_t, int64_t, Rl,               \
-                                          const V2<Rl> *, const V2<Rl> *, const V2<Rl> *,        \
-                                          const V2<Rl> *, const V2<Rl> *, cudaStream_t);
+                                          const TW<Rl> *, const TW<Rl> *, const TW<Rl> *,        \
+                                          cudaStream_t);
 PSS_INST(float)
 PSS_INST(double)
 

@@ -29,7 +29,7 @@ inline cudaError_t allow_smem(K kernel, size_t bytes, std::atomic<unsigned> &don
 }
 
 template <class Rl, int N, class Op>
-inline cudaError_t launch_row_n(Op op, const V2<Rl> *tw, int64_t rows_total, cudaStream_t s)
+inline cudaError_t launch_row_n(Op op, const TW<Rl> *tw, int64_t rows_total, cudaStream_t s)
 {
     using C = RowCfg<Rl, N>;
     auto k = k_row<Rl, N, Op>;
@@ -43,7 +43,7 @@ inline cudaError_t launch_row_n(Op op, const V2<Rl> *tw, int64_t rows_total, cud
 }
 
 template <class Rl, int N, class Op>
-inline cudaError_t launch_col_n(Op op, const V2<Rl> *tw, int64_t nx, int64_t batch, cudaStream_t s)
+inline cudaError_t launch_col_n(Op op, const TW<Rl> *tw, int64_t nx, int64_t batch, cudaStream_t s)
 {
     using C = ColCfg<Rl, N>;
     auto k = k_col<Rl, N, Op>;
@@ -57,7 +57,7 @@ inline cudaError_t launch_col_n(Op op, const V2<Rl> *tw, int64_t nx, int64_t bat
 
 // Row pass over every row of a [batch][ny][nx] array: transform length nx.
 template <class Rl, class Op>
-inline cudaError_t launch_row(int64_t nx, Op op, const V2<Rl> *tw, int64_t rows_total, cudaStream_t s)
+inline cudaError_t launch_row(int64_t nx, Op op, const TW<Rl> *tw, int64_t rows_total, cudaStream_t s)
 {
     switch (nx) {
 #define PSS_CASE(N) \
@@ -70,7 +70,7 @@ inline cudaError_t launch_row(int64_t nx, Op op, const V2<Rl> *tw, int64_t rows_
 
 // Column pass over every column of a [batch][ny][nx] array: transform length ny.
 template <class Rl, class Op>
-inline cudaError_t launch_col(int64_t ny, int64_t nx, Op op, const V2<Rl> *tw, int64_t batch,
+inline cudaError_t launch_col(int64_t ny, int64_t nx, Op op, const TW<Rl> *tw, int64_t batch,
                               cudaStream_t s)
 {
     switch (ny) {

@@ -86,7 +86,7 @@ template <class Rl, int N> struct ColCfg {
 // rows_total = batch * ny; row r of the batch starts at element r * NX
 template <class Rl, int N, class Op>
 __global__ void __launch_bounds__(RowCfg<Rl, N>::THREADS)
-    k_row(Op op, const V2<Rl> *__restrict__ tw, int64_t rows_total)
+    k_row(Op op, const TW<Rl> *__restrict__ tw, int64_t rows_total)
 {
     using C = RowCfg<Rl, N>;
     using V = V2<Rl>;
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(RowCfg<Rl, N>::THREADS)
 // grid (NX / W, batch); column x of field b
 template <class Rl, int N, class Op>
 __global__ void __launch_bounds__(ColCfg<Rl, N>::THREADS)
-    k_col(Op op, const V2<Rl> *__restrict__ tw)
+    k_col(Op op, const TW<Rl> *__restrict__ tw)
 {
     using C = ColCfg<Rl, N>;
     using V = V2<Rl>;
@@ -136,7 +136,7 @@ template <class Rl, int DIR> struct RowFft {
     Rl scale;  // applied after the transform when != 1
     template <int N, int P, bool BLOCK, class Sm>
     __device__ __forceinline__ void run(int64_t row, bool ok, int t, const Sm &sm,
-                                        const V2<Rl> *tw) const
+                                        const TW<Rl> *tw) const
     {
         constexpr int T = N / P;
         V2<Rl> v[P];
@@ -156,7 +156,7 @@ template <class Rl, int DIR> struct ColFft {
     Rl scale;
     template <int N, int P, bool BLOCK, class Sm>
     __device__ __forceinline__ void run(int64_t field, int x, int t, const Sm &sm,
-                                        const V2<Rl> *tw) const
+                                        const TW<Rl> *tw) const
     {
         constexpr int T = N / P;
         V2<Rl> v[P];

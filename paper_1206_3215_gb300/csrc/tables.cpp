@@ -70,13 +70,21 @@ void unit_pair_f32(double c, double s, float *fc, float *fs)
     *fs = bs;
 }
 
+void hilo_f32(double re, double im, float *out4)
+{
+    out4[0] = float(re);
+    out4[1] = float(im);
+    out4[2] = float(re - double(out4[0]));
+    out4[3] = float(im - double(out4[1]));
+}
+
 std::vector<float> twiddles_f32(int64_t n)
 {
-    std::vector<float> t(2 * size_t(n));
+    std::vector<float> t(4 * size_t(n));
     for (int64_t e = 0; e < n; ++e) {
         double c, s;
         cis_2pi(e, n, &c, &s);
-        unit_pair_f32(c, -s, &t[2 * e], &t[2 * e + 1]);
+        hilo_f32(c, -s, &t[4 * e]);
     }
     return t;
 }

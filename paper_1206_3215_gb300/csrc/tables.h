@@ -17,7 +17,12 @@ double wavenumber(int64_t m, int64_t n, double L);
 // squared modulus is closest to 1 (ties: nearest to (c, s)).
 void unit_pair_f32(double c, double s, float *fc, float *fs);
 
-// Twiddle table W_n^e = exp(-2 pi i e / n), e = 0..n-1, interleaved (re, im).
+// (re, im) as FP32 hi + lo: out4 = {hi.re, hi.im, lo.re, lo.im}, hi the
+// nearest float and lo the rounded residual.
+void hilo_f32(double re, double im, float *out4);
+
+// Twiddle table W_n^e = exp(-2 pi i e / n), e = 0..n-1: FP32 as hi + lo
+// quadruples (4 floats per entry), FP64 as (re, im) pairs.
 std::vector<float> twiddles_f32(int64_t n);
 std::vector<double> twiddles_f64(int64_t n);
 

@@ -50,7 +50,8 @@ def test_fft2d_round_trip_and_single_mode(lib, orc, cuda_device, precision):
     h = t.cpu().numpy()[0]
     expect = np.zeros((ny, nx), complex)
     expect[5, 200] = nx * ny
-    assert np.abs(h - expect).max() <= 50 * EPS[precision] * nx * ny
+    # zero outputs collect rounding from all nx*ny terms of magnitude 1
+    assert np.abs(h - expect).max() <= 64 * EPS[precision] * math.log2(nx * ny) * nx * ny
     lib.pss_fft2d(t.data_ptr(), nx, ny, 1, prec, +1, s)
     assert rel_l2(t.cpu().numpy()[0], mode) <= 8 * EPS[precision] * math.log2(nx * ny)
 
