@@ -218,7 +218,10 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated stream: the library enqueues on it and the events below are
+    # recorded on it (a NULL handle would make the library create its own)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     n, B = args.n, args.batch
 
     # per-rank fields (replicas: independent problems per GPU)
