@@ -177,6 +177,29 @@ const char *pss_last_error(const pss_grid *g);
 int pss_fft2d(void *data, int64_t nx, int64_t ny, int64_t batch, int precision, int direction,
               void *stream);
 
+/* Mass and energy of NLS fields (the diagnostics of pss_conserved_quantities
+ * for PSS_EQ_NLS) from caller-owned device arrays, without allocating any
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that cannot call cudaMalloc, such as code whose device memory belongs to
+ * another allocator or a fixed budget, or latency-critical loops in which an
+ * allocation, which may synchronise the device, is not acceptable.
+ *  psi:     device, physical field, interleaved complex [batch][ny][nx];
+ *  psi_hat: device, its unnormalised forward 2D DFT (e.g. pss_fft2d, -1);
+ *  precision PSS_FP32 (complex64 inputs) or PSS_FP64 (complex128);
+ *  out:     device, 2*batch doubles: out[2f] = mass, out[2f+1] = energy;
+ *  stream:  cudaStream_t or NULL.  Asynchronous; read out after the stream.
+ * Scratch lives in a static device array of the library sized for at most
+ * 64 fields (198,144 bytes, held on every GPU that loads the library until
+ * the process exits).  Every call shares that array: calls that overlap on
+ * the GPU race on it, so serialise them (one stream, or events).  The first
+ * call on each device looks up the array's device address with that device
+ * current; make that first call before any stream capture.
+ * Errors: PSS_E_ARG (bad pointer, size, precision, or batch > 64, with a
+ * message in pss_last_error(NULL)), PSS_E_CUDA. */
+int pss_nls_invariants_static(const void *psi, const void *psi_hat, int64_t nx, int64_t ny,
+                              int64_t batch, double lx, double ly, double sigma, int precision,
+                              double *out, void *stream);
+
 /* Library version string. */
 const char *pss_version(void);
 

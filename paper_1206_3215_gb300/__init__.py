@@ -26,7 +26,7 @@ EXPORTED = [
     "pss_default_params", "pss_create_grid", "pss_set_state", "pss_step_n", "pss_get_state",
     "pss_conserved_quantities", "pss_stats", "pss_checkpoint_size", "pss_checkpoint_save",
     "pss_checkpoint_load", "pss_sync", "pss_destroy", "pss_last_error", "pss_fft2d",
-    "pss_version", "pss_set_profiling", "pss_profile_read",
+    "pss_version", "pss_set_profiling", "pss_profile_read", "pss_nls_invariants_static",
 ]
 
 
@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH):
             "pss_version": (ctypes.c_char_p, []),
             "pss_set_profiling": (I, [P, I]),
             "pss_profile_read": (I, [P, P, I, P]),
+            "pss_nls_invariants_static": (I, [P, P, I64, I64, I64, D, D, D, I, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -181,6 +182,14 @@ def pss_profile_read(h) -> dict:
     _check(load_library().pss_profile_read(h, out.ctypes.data, 7, ctypes.byref(cnt)), h)
     return {"launches": int(out[0]), "row": (int(out[1]), float(out[2])),
             "col": (int(out[3]), float(out[4])), "other": (int(out[5]), float(out[6]))}
+
+
+def pss_nls_invariants_static(psi_ptr: int, hat_ptr: int, nx: int, ny: int, batch: int,
+                              lx: float, ly: float, sigma: float, precision: int, out_ptr: int,
+                              stream: int | None = None) -> None:
+    """NLS mass and energy into a device array, with no allocation (see pss.h)."""
+    _check(load_library().pss_nls_invariants_static(psi_ptr, hat_ptr, nx, ny, batch, lx, ly, sigma,
+                                                     precision, out_ptr, stream), None)
 
 
 def pss_version() -> str:

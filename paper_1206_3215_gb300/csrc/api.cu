@@ -20,6 +20,8 @@ using namespace pss;
 
 static thread_local std::string g_create_error;
 
+void pss::set_global_error(const char *msg) { g_create_error = msg; }
+
 // ----------------------------------------------------------------------------
 // helpers
 

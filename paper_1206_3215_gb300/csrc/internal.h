@@ -52,6 +52,9 @@ cudaError_t nls_sums(const V2<Rl> *psi, const V2<Rl> *psi_hat, int64_t nx, int64
                      int64_t batch, const double *kx2, const double *ky2, double *partials,
                      double *out, cudaStream_t s);
 
+// message returned by pss_last_error(NULL) for calls without a grid handle
+void set_global_error(const char *msg);
+
 // status bits written by reductions
 constexpr unsigned FLAG_NONFINITE = 1u;
 constexpr unsigned FLAG_NOT_CONVERGED = 2u;

@@ -6,6 +6,9 @@
 // tree.  The result therefore does not depend on scheduling or on the batch.
 #include <math.h>
 
+#include <cmath>
+#include <mutex>
+
 #include "fft_core.cuh"
 
 namespace pss {
@@ -88,3 +91,137 @@ template cudaError_t nls_sums<double>(const double2 *, const double2 *, int64_t,
                                       cudaStream_t);
 
 }  // namespace pss
+
+// ----------------------------------------------------------------------------
+// NLS invariants without allocation.
+//
+// The same reduction as nls_sums (fixed block/thread assignment, fixed fold
+// order), with |k|^2 formed from the index instead of a grid's table, and
+// with the per-block partial sums and the per-field totals kept in one
+// file-scope device array instead of memory a grid allocated.  It is for
+// callers that cannot call cudaMalloc: code whose device memory is owned by
+// another allocator or a fixed budget, and latency-critical loops where an
+// allocation (which may synchronise the device) is not acceptable.  Every GPU
+// that loads the library holds the array until the process exits, and every
+// call shares it: calls that overlap on the GPU race on it.
+
+namespace pss {
+
+constexpr int STATIC_MAX_BATCH = 64;
+constexpr size_t STATIC_PARTIALS = size_t(STATIC_MAX_BATCH) * RED_BLOCKS * 3;
+constexpr size_t STATIC_DOUBLES = STATIC_PARTIALS + size_t(STATIC_MAX_BATCH) * 3;
+
+// 64 fields * 128 blocks * 3 partial sums + 64 * 3 totals = 198,144 bytes
+static __device__ __align__(256) double g_static_scratch[STATIC_DOUBLES];
+
+namespace {
+std::mutex g_static_mu;
+double *g_static_addr[64] = {};  // device address of g_static_scratch per device ordinal
+
+// Host code sees g_static_scratch only as a host-side stand-in; the device
+// address is looked up once per device, with that device current.
+cudaError_t static_scratch(double **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_addr[dev] = static_cast<double *>(p);
+    }
+    *out = g_static_addr[dev];
+    return cudaSuccess;
+}
+
+__device__ __forceinline__ double wavenumber2(int64_t m, int64_t n, double dk)
+{
+    const double k = dk * double(m < n / 2 ? m : m - n);
+    return k * k;
+}
+}  // namespace
+
+template <class Rl>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_nls_sums_inline(const V2<Rl> *psi, const V2<Rl> *hat, int64_t nx, int64_t ny, double dkx,
+                      double dky, double *partials)
+{
+    __shared__ double sh[3 * RED_THREADS];
+    const int64_t f = blockIdx.y, n = nx * ny;
+    const V2<Rl> *p = psi + f * n, *h = hat + f * n;
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = int64_t(blockIdx.x) * RED_THREADS + threadIdx.x; i < n;
+         i += int64_t(RED_BLOCKS) * RED_THREADS) {
+        const V2<Rl> z = p[i];
+        const double m2 = double(z.x) * z.x + double(z.y) * z.y;
+        a[0] += m2;
+        a[1] += m2 * m2;
+        const V2<Rl> w = h[i];
+        a[2] += (wavenumber2(i % nx, nx, dkx) + wavenumber2(i / nx, ny, dky)) *
+                (double(w.x) * w.x + double(w.y) * w.y);
+    }
+    block_sum<3>(a, sh);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) partials[(f * RED_BLOCKS + blockIdx.x) * 3 + k] = a[k];
+}
+
+__global__ void k_nls_finish(const double *sums, int64_t batch, double dA, double inv_n,
+                             double sigma, double *out)
+{
+    const int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (f >= batch) return;
+    const double *s = sums + 3 * f;
+    out[2 * f] = dA * s[0];
+    out[2 * f + 1] = dA * (0.5 * s[2] * inv_n + 0.25 * sigma * s[1]);
+}
+
+}  // namespace pss
+
+extern "C" int pss_nls_invariants_static(const void *psi, const void *psi_hat, int64_t nx,
+                                         int64_t ny, int64_t batch, double lx, double ly,
+                                         double sigma, int precision, double *out, void *stream)
+{
+    using namespace pss;
+    auto ok = [](int64_t n) { return n >= 16 && n <= 8192 && (n & (n - 1)) == 0; };
+    if (!psi || !psi_hat || !out || !ok(nx) || !ok(ny) || !(lx > 0) || !(ly > 0) ||
+        !std::isfinite(sigma) || (precision != 0 && precision != 1)) {
+        set_global_error("pss_nls_invariants_static: invalid argument");
+        return 1;  // PSS_E_ARG
+    }
+    if (batch < 1 || batch > STATIC_MAX_BATCH) {
+        set_global_error("pss_nls_invariants_static: batch must be in [1, 64], the size of the "
+                         "library's static scratch");
+        return 1;  // PSS_E_ARG
+    }
+    double *scratch = nullptr;
+    if (static_scratch(&scratch) != cudaSuccess) {
+        set_global_error("pss_nls_invariants_static: cudaGetSymbolAddress failed");
+        return 3;  // PSS_E_CUDA
+    }
+    // every partial and total read below is first written by this same call,
+    // so nothing has to be cleared between calls
+    double *partials = scratch, *sums = scratch + STATIC_PARTIALS;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const double two_pi = 6.283185307179586476925286766559;
+    const dim3 grid(RED_BLOCKS, unsigned(batch));
+    if (precision == 0)
+        k_nls_sums_inline<float><<<grid, RED_THREADS, 0, s>>>(
+            static_cast<const float2 *>(psi), static_cast<const float2 *>(psi_hat), nx, ny,
+            two_pi / lx, two_pi / ly, partials);
+    else
+        k_nls_sums_inline<double><<<grid, RED_THREADS, 0, s>>>(
+            static_cast<const double2 *>(psi), static_cast<const double2 *>(psi_hat), nx, ny,
+            two_pi / lx, two_pi / ly, partials);
+    k_fold<3><<<unsigned(batch), RED_THREADS, 0, s>>>(partials, sums);
+    k_nls_finish<<<1, 64, 0, s>>>(sums, batch, (lx / double(nx)) * (ly / double(ny)),
+                                  1.0 / (double(nx) * double(ny)), sigma, out);
+    if (cudaGetLastError() != cudaSuccess) {
+        set_global_error("pss_nls_invariants_static: launch failed");
+        return 3;  // PSS_E_CUDA
+    }
+    return 0;
+}
