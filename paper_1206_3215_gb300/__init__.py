@@ -15,7 +15,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpss.so")
+LIB_PATH = os.environ.get("PSS_LIBRARY", os.path.join(_HERE, "libpss.so"))
 
 PSS_OK, PSS_E_ARG, PSS_E_OOM, PSS_E_CUDA, PSS_E_NOT_CONVERGED, PSS_E_NONFINITE, PSS_E_STATE = range(7)
 PSS_EQ_NLS, PSS_EQ_SG, PSS_EQ_NS = 0, 1, 2

@@ -36,8 +36,8 @@ def headers() -> list[str]:
     return hs + [os.path.join(os.path.dirname(HERE), "include", "pss.h")]
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(OUT, os.path.basename(src) + ".o")
+def _compile(src: str, extra: list[str], objdir: str = OUT) -> str:
+    obj = os.path.join(objdir, os.path.basename(src) + ".o")
     newest_dep = max(os.path.getmtime(p) for p in [src] + headers())
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep:
         return obj
@@ -49,23 +49,27 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(force: bool = False, jobs: int | None = None, extra: list[str] | None = None) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, jobs: int | None = None, extra: list[str] | None = None,
+          lib: str = LIB, objdir: str = OUT) -> str:
+    """Compile every csrc/ translation unit and link `lib`.  `extra` adds nvcc
+    flags (e.g. -DPSS_COL_P=8 for another launch shape) and should come with
+    its own `objdir` and `lib`."""
+    os.makedirs(objdir, exist_ok=True)
     if force:
-        for f in os.listdir(OUT):
-            os.remove(os.path.join(OUT, f))
+        for f in os.listdir(objdir):
+            os.remove(os.path.join(objdir, f))
     srcs = sources()
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra or []), srcs))
-    if (not os.path.exists(LIB)) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
+        objs = list(ex.map(lambda s: _compile(s, extra or [], objdir), srcs))
+    if (not os.path.exists(lib)) or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in objs):
+        tmp = lib + f".{os.getpid()}.tmp"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -142,9 +142,14 @@ template <int RAD, int DIR, int S, class V> __device__ __forceinline__ void dft_
 }
 
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
-__host__ __device__ constexpr int bitrev(int r, int bits)
+// bit reversal of the low `bits` bits of r; a loop (not recursion) so that it
+// folds to a constant inside unrolled loops and register arrays stay in
+// registers
+__host__ __device__ __forceinline__ constexpr int bitrev(int r, int bits)
 {
-    return bits == 0 ? 0 : ((r & 1) << (bits - 1)) | bitrev(r >> 1, bits - 1);
+    int o = 0;
+    for (int i = 0; i < bits; ++i) o = (o << 1) | ((r >> i) & 1);
+    return o;
 }
 
 // Stage list of a length-N transform with P points per thread.
@@ -166,6 +171,32 @@ template <class V, int PADLOG> struct SmemLine {
     __device__ __forceinline__ V &operator[](int i) const { return base[i + (i >> PADLOG)]; }
 };
 
+// The twiddle loads of a stage do not depend on the data, so the compiler
+// would issue those of every stage of every transform in a kernel up front
+// and hold them all in registers (hundreds for the two transforms of a fused
+// pass).  Passing the table pointer through a volatile move after the
+// stage's exchange barrier keeps each stage's loads after that barrier.
+template <class W> __device__ __forceinline__ const W *launder(const W *p)
+{
+    const W *q;
+    asm volatile("mov.b64 %0, %1;" : "=l"(q) : "l"(p));
+    return q;
+}
+
+// Register fence: every value of v is materialised here and nothing that
+// uses v moves above it, so the two transforms of a fused pass are not
+// interleaved (which would keep both transforms' temporaries live).
+template <int P> __device__ __forceinline__ void fence(float2 (&v)[P])
+{
+#pragma unroll
+    for (int m = 0; m < P; ++m) asm volatile("" : "+f"(v[m].x), "+f"(v[m].y));
+}
+template <int P> __device__ __forceinline__ void fence(double2 (&v)[P])
+{
+#pragma unroll
+    for (int m = 0; m < P; ++m) asm volatile("" : "+d"(v[m].x), "+d"(v[m].y));
+}
+
 template <bool BLOCK> __device__ __forceinline__ void fft_sync()
 {
     if constexpr (BLOCK) __syncthreads();
@@ -184,6 +215,7 @@ __device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const 
     constexpr bool LAST = (S == PL::STAGES - 1);
     if constexpr (S > 0) {
         // twiddles W_{NS R}^{(j mod NS) r} = W_N^{(j mod NS) r N/(NS R)}
+        tw = launder(tw);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int jm = (t + q * T) & (NS - 1);

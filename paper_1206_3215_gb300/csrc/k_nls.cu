@@ -15,17 +15,20 @@ __device__ __forceinline__ void sincos_(float a, float *s, float *c) { sincosf(a
 __device__ __forceinline__ void sincos_(double a, double *s, double *c) { sincos(a, s, c); }
 
 template <class Rl> struct NlsRow {
+    static constexpr int NIN = 1;
     V2<Rl> *data;
     Rl sigma_dt;
+    __device__ const V2<Rl> *in(int) const { return data; }
     template <int N, int P, bool BLOCK, class Sm>
-    __device__ __forceinline__ void run(int64_t row, bool ok, int t, const Sm &sm,
-                                        const TW<Rl> *tw) const
+    __device__ __forceinline__ void row(V2<Rl> (&vv)[1][P], int64_t row, bool ok, int t,
+                                        const Sm (&smm)[1], const TW<Rl> *tw) const
     {
         constexpr int T = N / P;
-        V2<Rl> v[P];
+        V2<Rl>(&v)[P] = vv[0];
+        const Sm &sm = smm[0];
         V2<Rl> *p = data + row * N;
-        load_line<P, T>(v, p, 1, t, ok);
         block_fft<N, P, +1, BLOCK>(v, sm, t, tw);
+        fence(v);
 #pragma unroll
         for (int m = 0; m < P; ++m) {
             // psi exp(-i th) = psi + psi (cos th - 1 - i sin th), with
@@ -39,6 +42,7 @@ template <class Rl> struct NlsRow {
             v[m].x = x + (x * cm1 + y * sn);
             v[m].y = y + (y * cm1 - x * sn);
         }
+        fence(v);
         block_fft<N, P, -1, BLOCK>(v, sm, t, tw);
         store_line<P, T>(v, p, 1, t, ok);
     }
@@ -56,26 +60,31 @@ template <class V, class W> __device__ __forceinline__ V apply_km1(V z, W km1)
 }
 
 template <class Rl> struct NlsCol {
+    static constexpr int NIN = 1;
     V2<Rl> *data;
     int64_t nx;
     Rl scale;
     const TW<Rl> *ax, *by;  // exp(-i kx^2 tau) - 1, exp(-i ky^2 tau) - 1
+    __device__ const V2<Rl> *in(int) const { return data; }
     template <int N, int P, bool BLOCK, class Sm>
-    __device__ __forceinline__ void run(int64_t field, int x, int t, const Sm &sm,
-                                        const TW<Rl> *tw) const
+    __device__ __forceinline__ void col(V2<Rl> (&vv)[1][P], int64_t field, int x, int t,
+                                        const Sm (&smm)[1], const TW<Rl> *tw) const
     {
         constexpr int T = N / P;
-        V2<Rl> v[P];
+        V2<Rl>(&v)[P] = vv[0];
+        const Sm &sm = smm[0];
         V2<Rl> *p = data + field * N * nx + x;
-        load_line<P, T>(v, p, nx, t, true);
         block_fft<N, P, -1, BLOCK>(v, sm, t, tw);
+        fence(v);
         const TW<Rl> a = __ldg(ax + x);
+        const TW<Rl> *byl = launder(by);  // keep these loads after the transform
 #pragma unroll
         for (int m = 0; m < P; ++m) {
             // scale is a power of two: exact
             const V2<Rl> z = apply_km1(cscale(v[m], scale), a);
-            v[m] = apply_km1(z, __ldg(by + t + T * m));
+            v[m] = apply_km1(z, __ldg(byl + t + T * m));
         }
+        fence(v);
         block_fft<N, P, +1, BLOCK>(v, sm, t, tw);
         store_line<P, T>(v, p, nx, t, true);
     }

@@ -28,30 +28,59 @@ inline cudaError_t allow_smem(K kernel, size_t bytes, std::atomic<unsigned> &don
     return e;
 }
 
+// Persistent grid: as many CTAs as fit on the device at once (occupancy of
+// this kernel instance, cached per device), never more than there are tiles.
+template <class K> inline cudaError_t resident_ctas(K kernel, int threads, size_t smem,
+                                                    int (&cache)[32], int *out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int &c = cache[dev & 31];
+    if (c == 0) {
+        int per_sm = 0, sms = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem)) != cudaSuccess)
+            return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        c = (per_sm > 0 ? per_sm : 1) * sms;
+    }
+    *out = c;
+    return cudaSuccess;
+}
+
 template <class Rl, int N, class Op>
 inline cudaError_t launch_row_n(Op op, const TW<Rl> *tw, int64_t rows_total, cudaStream_t s)
 {
-    using C = RowCfg<Rl, N>;
+    using C = RowCfg<Rl, N, Op::NIN>;
     auto k = k_row<Rl, N, Op>;
     static std::atomic<unsigned> done{0};
+    static int ctas[32] = {};
     cudaError_t e = allow_smem(k, C::SMEM, done);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = (rows_total + C::ROWS - 1) / C::ROWS;
-    if (blocks <= 0) return cudaSuccess;
-    k<<<dim3(unsigned(blocks)), C::THREADS, C::SMEM, s>>>(op, tw, rows_total);
+    const int64_t tiles = (rows_total + C::ROWS - 1) / C::ROWS;
+    if (tiles <= 0) return cudaSuccess;
+    int grid = 0;
+    if ((e = resident_ctas(k, C::THREADS, C::SMEM, ctas, &grid)) != cudaSuccess) return e;
+    if (tiles < grid) grid = int(tiles);
+    k<<<dim3(unsigned(grid)), C::THREADS, C::SMEM, s>>>(op, tw, rows_total);
     return cudaGetLastError();
 }
 
 template <class Rl, int N, class Op>
 inline cudaError_t launch_col_n(Op op, const TW<Rl> *tw, int64_t nx, int64_t batch, cudaStream_t s)
 {
-    using C = ColCfg<Rl, N>;
+    using C = ColCfg<Rl, N, Op::NIN>;
     auto k = k_col<Rl, N, Op>;
     static std::atomic<unsigned> done{0};
+    static int ctas[32] = {};
     cudaError_t e = allow_smem(k, C::SMEM, done);
     if (e != cudaSuccess) return e;
-    if (batch <= 0) return cudaSuccess;
-    k<<<dim3(unsigned(nx / C::W), unsigned(batch)), C::THREADS, C::SMEM, s>>>(op, tw);
+    const int64_t tiles = (nx / C::W) * batch;
+    if (tiles <= 0) return cudaSuccess;
+    int grid = 0;
+    if ((e = resident_ctas(k, C::THREADS, C::SMEM, ctas, &grid)) != cudaSuccess) return e;
+    if (tiles < grid) grid = int(tiles);
+    k<<<dim3(unsigned(grid)), C::THREADS, C::SMEM, s>>>(op, tw, nx, batch);
     return cudaGetLastError();
 }
 

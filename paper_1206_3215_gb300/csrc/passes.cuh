@@ -1,39 +1,70 @@
 // Row and column pass kernels.
 //
-// A row pass transforms along x (contiguous rows of length NX); a CTA holds
-// ROWS rows, each carried by T = NX/P threads.  A column pass transforms along
-// y; a CTA holds W adjacent columns of length NY, thread (c, t) with the column
-// index c fastest so that a warp's loads cover 32/W rows of W contiguous
-// points.  The equation-specific work is an "op" that loads its inputs, calls
-// block_fft around its pointwise or k-space arithmetic and stores its outputs,
-// so each pass is exactly one read and one write of every array it touches.
+// A row pass transforms along x (contiguous rows of length NX); a tile is
+// ROWS rows, each carried by T = NX/P threads.  A column pass transforms
+// along y; a tile is W adjacent columns of one field, thread (c, t) with the
+// column index c fastest so that a warp's accesses cover 32/W rows of W
+// contiguous points.
+//
+// Both are persistent: each CTA walks tiles blockIdx.x, +gridDim.x, ...  While
+// it transforms one tile, cp.async copies of the next tile's input lines are
+// in flight into the other of two shared-memory buffers, so HBM stays busy
+// during the arithmetic without holding the data in registers.  Each thread
+// copies exactly the points it reads back for the first Stockham stage
+// (element t + T m of its line), so it only waits for its own copies; the
+// buffer then serves as the exchange space of that tile's transforms.
+//
+// The equation-specific work is an "op": it names its staged input arrays
+// and, given the staged points in registers, does the transforms around its
+// pointwise or k-space arithmetic and stores its outputs, so each pass is
+// one read and one write of every array it touches.
 #pragma once
 #include "fft_core.cuh"
 
 namespace pss {
 
 // ----------------------------------------------------------------------------
-// Per (precision, length) launch shapes.
+// Per (precision, length) launch shapes.  The PSS_* macros let a build pick
+// other shapes (points per thread, threads per CTA, resident CTAs per SM).
+#ifndef PSS_ROW_P
+#define PSS_ROW_P 16
+#endif
+#ifndef PSS_COL_P
+#define PSS_COL_P 16
+#endif
+#ifndef PSS_ROW_THREADS
+#define PSS_ROW_THREADS 256
+#endif
+#ifndef PSS_COL_THREADS
+#define PSS_COL_THREADS 256
+#endif
+#ifndef PSS_MIN_CTAS
+#define PSS_MIN_CTAS 1
+#endif
 template <class Rl> struct Shape {
     static constexpr int ESZ = 2 * int(sizeof(Rl));
     // points per thread of the row and column transforms
-    __host__ __device__ static constexpr int rowP(int n) { return n < 16 ? n : 16; }
-    __host__ __device__ static constexpr int colP(int n) { return n < 16 ? n : 16; }
-    // rows per CTA: about 256 threads
+    __host__ __device__ static constexpr int rowP(int n) { return n < PSS_ROW_P ? n : PSS_ROW_P; }
+    __host__ __device__ static constexpr int colP(int n) { return n < PSS_COL_P ? n : PSS_COL_P; }
+    // rows per tile: about PSS_ROW_THREADS threads per CTA
     __host__ __device__ static constexpr int rows(int n)
     {
-        return (n / rowP(n)) >= 256 ? 1 : 256 / (n / rowP(n));
+        return (n / rowP(n)) >= PSS_ROW_THREADS ? 1 : PSS_ROW_THREADS / (n / rowP(n));
     }
-    // columns per CTA: 64-byte row segments when shared memory and the
-    // register budget (512 threads FP32, 256 FP64) allow
+    // columns per tile: 64-byte row segments (FP32) when the thread budget
+    // and shared memory (two buffers) allow
     __host__ __device__ static constexpr int cols(int n)
     {
         int w = sizeof(Rl) == 4 ? 8 : 4;
-        const int tmax = sizeof(Rl) == 4 ? 512 : 256;
-        while (w > 1 && ((long)w * (n + n / 16) * ESZ > 150 * 1024 || w * (n / colP(n)) > tmax)) w /= 2;
+        while (w > 1 && ((long)2 * w * (n + n / 16) * ESZ > 200 * 1024L ||
+                         w * (n / colP(n)) > PSS_COL_THREADS))
+            w /= 2;
         return w;
     }
 };
+
+// dynamic shared memory a pass may use per CTA (the GB300 limit is 227 KB)
+constexpr size_t SMEM_LIMIT = 200 * 1024;
 
 // shared-memory pad period of a transform with P points per thread
 __host__ __device__ constexpr int pad_log(int P) { return P < 2 ? 30 : ilog2(P); }
@@ -62,63 +93,168 @@ __host__ __device__ constexpr int col_stride(int base, int W, int ESZ)
     return best;
 }
 
-template <class Rl, int N> struct RowCfg {
+template <class Rl, int N, int NIN> struct RowCfg {
     static constexpr int P = Shape<Rl>::rowP(N), T = N / P, ROWS = Shape<Rl>::rows(N);
     static constexpr int PADLOG = pad_log(P);
     static constexpr int LINE = N + (N >> PADLOG);
     static constexpr int THREADS = ROWS * T;
     static constexpr bool BLOCK = T > 32;
-    static constexpr size_t SMEM = (T > 1) ? size_t(ROWS) * LINE * Shape<Rl>::ESZ : 0;
+    // two buffers of NIN input lines per row (one when two do not fit)
+    static constexpr int BUF = NIN * ROWS * LINE;
+    static constexpr int NBUF = size_t(2) * BUF * Shape<Rl>::ESZ <= SMEM_LIMIT ? 2 : 1;
+    static constexpr size_t SMEM = size_t(NBUF) * BUF * Shape<Rl>::ESZ;
 };
 
-template <class Rl, int N> struct ColCfg {
+template <class Rl, int N, int NIN> struct ColCfg {
     static constexpr int P = Shape<Rl>::colP(N), T = N / P, W = Shape<Rl>::cols(N);
     static constexpr int PADLOG = pad_log(P);
     static constexpr int STRIDE = col_stride(N + (N >> PADLOG), W, Shape<Rl>::ESZ);
     static constexpr int THREADS = W * T;
     static constexpr bool BLOCK = THREADS > 32;
-    static constexpr size_t SMEM = (T > 1) ? size_t(W) * STRIDE * Shape<Rl>::ESZ : 0;
+    static constexpr int BUF = NIN * W * STRIDE;
+    static constexpr int NBUF = size_t(2) * BUF * Shape<Rl>::ESZ <= SMEM_LIMIT ? 2 : 1;
+    static constexpr size_t SMEM = size_t(NBUF) * BUF * Shape<Rl>::ESZ;
 };
+
+// ----------------------------------------------------------------------------
+// cp.async: per-thread asynchronous global -> shared copies (no registers held)
+
+template <int BYTES> __device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src)
+{
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem_src), "n"(BYTES)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Stage P points of a line (element t + T m at stride st) into a padded
+// shared line at the same positions.
+template <int P, int T, class V, class Sm>
+__device__ __forceinline__ void stage_line(const Sm &sm, const V *__restrict__ src, int64_t st, int t)
+{
+#pragma unroll
+    for (int m = 0; m < P; ++m) cp_async<sizeof(V)>(&sm[t + T * m], src + int64_t(t + T * m) * st);
+}
+template <int P, int T, class V, class Sm>
+__device__ __forceinline__ void read_line(V (&v)[P], const Sm &sm, int t)
+{
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = sm[t + T * m];
+}
 
 // ----------------------------------------------------------------------------
 // Kernel shells
 
 // rows_total = batch * ny; row r of the batch starts at element r * NX
 template <class Rl, int N, class Op>
-__global__ void __launch_bounds__(RowCfg<Rl, N>::THREADS)
+__global__ void __launch_bounds__(RowCfg<Rl, N, Op::NIN>::THREADS, PSS_MIN_CTAS)
     k_row(Op op, const TW<Rl> *__restrict__ tw, int64_t rows_total)
 {
-    using C = RowCfg<Rl, N>;
+    using C = RowCfg<Rl, N, Op::NIN>;
     using V = V2<Rl>;
+    using Sm = SmemLine<V, C::PADLOG>;
+    constexpr int NIN = Op::NIN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *const buf = reinterpret_cast<V *>(smem_raw);
     const int lr = threadIdx.x / C::T, t = threadIdx.x % C::T;
-    SmemLine<V, C::PADLOG> sm{reinterpret_cast<V *>(smem_raw) + lr * C::LINE};
-    const int64_t row = int64_t(blockIdx.x) * C::ROWS + lr;
-    op.template run<N, C::P, C::BLOCK>(row, row < rows_total, t, sm, tw);
+    const int64_t tiles = (rows_total + C::ROWS - 1) / C::ROWS;
+
+    auto line = [&](int b, int k) { return Sm{buf + b * C::BUF + (k * C::ROWS + lr) * C::LINE}; };
+    auto issue = [&](int64_t tile, int b) {
+        const int64_t row = tile * C::ROWS + lr;
+        if (tile < tiles && row < rows_total)
+#pragma unroll
+            for (int k = 0; k < NIN; ++k) stage_line<C::P, C::T>(line(b, k), op.in(k) + row * N, 1, t);
+        cp_async_commit();
+    };
+
+    int64_t tile = blockIdx.x;
+    if (C::NBUF == 2) issue(tile, 0);
+    for (int it = 0; tile < tiles; ++it, tile += gridDim.x) {
+        int b = 0;
+        if constexpr (C::NBUF == 2) {
+            b = it & 1;
+            issue(tile + gridDim.x, b ^ 1);
+            cp_async_wait<1>();
+        } else {
+            issue(tile, 0);
+            cp_async_wait<0>();
+        }
+        const int64_t row = tile * C::ROWS + lr;
+        V v[NIN][C::P];
+        Sm sm[NIN];
+#pragma unroll
+        for (int k = 0; k < NIN; ++k) {
+            sm[k] = line(b, k);
+            read_line<C::P, C::T>(v[k], sm[k], t);
+        }
+        op.template row<N, C::P, C::BLOCK>(v, row, row < rows_total, t, sm, tw);
+        fft_sync<C::BLOCK>();  // this buffer is refilled by the next iteration's prefetch
+    }
+    cp_async_wait<0>();
 }
 
-// grid (NX / W, batch); column x of field b
+// tiles: (NX / W) column groups per field, fields in order
 template <class Rl, int N, class Op>
-__global__ void __launch_bounds__(ColCfg<Rl, N>::THREADS)
-    k_col(Op op, const TW<Rl> *__restrict__ tw)
+__global__ void __launch_bounds__(ColCfg<Rl, N, Op::NIN>::THREADS, PSS_MIN_CTAS)
+    k_col(Op op, const TW<Rl> *__restrict__ tw, int64_t nx, int64_t batch)
 {
-    using C = ColCfg<Rl, N>;
+    using C = ColCfg<Rl, N, Op::NIN>;
     using V = V2<Rl>;
+    using Sm = SmemLine<V, C::PADLOG>;
+    constexpr int NIN = Op::NIN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *const buf = reinterpret_cast<V *>(smem_raw);
     const int c = threadIdx.x % C::W, t = threadIdx.x / C::W;
-    SmemLine<V, C::PADLOG> sm{reinterpret_cast<V *>(smem_raw) + c * C::STRIDE};
-    op.template run<N, C::P, C::BLOCK>(int64_t(blockIdx.y), int(blockIdx.x) * C::W + c, t, sm, tw);
+    const int64_t groups = nx / C::W, tiles = groups * batch;
+
+    auto line = [&](int b, int k) { return Sm{buf + b * C::BUF + (k * C::W + c) * C::STRIDE}; };
+    auto issue = [&](int64_t tile, int b) {
+        if (tile < tiles) {
+            const int64_t field = tile / groups, x = (tile % groups) * C::W + c;
+#pragma unroll
+            for (int k = 0; k < NIN; ++k)
+                stage_line<C::P, C::T>(line(b, k), op.in(k) + field * N * nx + x, nx, t);
+        }
+        cp_async_commit();
+    };
+
+    int64_t tile = blockIdx.x;
+    if (C::NBUF == 2) issue(tile, 0);
+    for (int it = 0; tile < tiles; ++it, tile += gridDim.x) {
+        int b = 0;
+        if constexpr (C::NBUF == 2) {
+            b = it & 1;
+            issue(tile + gridDim.x, b ^ 1);
+            cp_async_wait<1>();
+        } else {
+            issue(tile, 0);
+            cp_async_wait<0>();
+        }
+        const int64_t field = tile / groups;
+        const int x = int((tile % groups) * C::W + c);
+        V v[NIN][C::P];
+        Sm sm[NIN];
+#pragma unroll
+        for (int k = 0; k < NIN; ++k) {
+            sm[k] = line(b, k);
+            read_line<C::P, C::T>(v[k], sm[k], t);
+        }
+        op.template col<N, C::P, C::BLOCK>(v, field, x, t, sm, tw);
+        fft_sync<C::BLOCK>();
+    }
+    cp_async_wait<0>();
 }
 
 // ----------------------------------------------------------------------------
-// Load/store helpers: register m <-> element t + T m of a line with stride ST
-template <int P, int T, class V>
-__device__ __forceinline__ void load_line(V (&v)[P], const V *__restrict__ p, int64_t st, int t,
-                                          bool ok)
-{
-#pragma unroll
-    for (int m = 0; m < P; ++m) v[m] = ok ? p[int64_t(t + T * m) * st] : V{0, 0};
-}
+// Store helper: register m -> element t + T m of a line with stride st
 template <int P, int T, class V>
 __device__ __forceinline__ void store_line(const V (&v)[P], V *__restrict__ p, int64_t st, int t,
                                            bool ok)
@@ -132,41 +268,37 @@ __device__ __forceinline__ void store_line(const V (&v)[P], V *__restrict__ p, i
 // Plain transforms (the 2D FFT of every step, Section 4)
 
 template <class Rl, int DIR> struct RowFft {
+    static constexpr int NIN = 1;
     V2<Rl> *data;
     Rl scale;  // applied after the transform when != 1
+    __device__ const V2<Rl> *in(int) const { return data; }
     template <int N, int P, bool BLOCK, class Sm>
-    __device__ __forceinline__ void run(int64_t row, bool ok, int t, const Sm &sm,
+    __device__ __forceinline__ void row(V2<Rl> (&v)[1][P], int64_t r, bool ok, int t, const Sm (&sm)[1],
                                         const TW<Rl> *tw) const
     {
-        constexpr int T = N / P;
-        V2<Rl> v[P];
-        V2<Rl> *p = data + row * N;
-        load_line<P, T>(v, p, 1, t, ok);
-        block_fft<N, P, DIR, BLOCK>(v, sm, t, tw);
+        block_fft<N, P, DIR, BLOCK>(v[0], sm[0], t, tw);
         if (scale != Rl(1))
 #pragma unroll
-            for (int m = 0; m < P; ++m) v[m] = cscale(v[m], scale);
-        store_line<P, T>(v, p, 1, t, ok);
+            for (int m = 0; m < P; ++m) v[0][m] = cscale(v[0][m], scale);
+        store_line<P, N / P>(v[0], data + r * N, 1, t, ok);
     }
 };
 
 template <class Rl, int DIR> struct ColFft {
+    static constexpr int NIN = 1;
     V2<Rl> *data;
     int64_t nx;
     Rl scale;
+    __device__ const V2<Rl> *in(int) const { return data; }
     template <int N, int P, bool BLOCK, class Sm>
-    __device__ __forceinline__ void run(int64_t field, int x, int t, const Sm &sm,
-                                        const TW<Rl> *tw) const
+    __device__ __forceinline__ void col(V2<Rl> (&v)[1][P], int64_t field, int x, int t,
+                                        const Sm (&sm)[1], const TW<Rl> *tw) const
     {
-        constexpr int T = N / P;
-        V2<Rl> v[P];
-        V2<Rl> *p = data + field * N * nx + x;
-        load_line<P, T>(v, p, nx, t, true);
-        block_fft<N, P, DIR, BLOCK>(v, sm, t, tw);
+        block_fft<N, P, DIR, BLOCK>(v[0], sm[0], t, tw);
         if (scale != Rl(1))
 #pragma unroll
-            for (int m = 0; m < P; ++m) v[m] = cscale(v[m], scale);
-        store_line<P, T>(v, p, nx, t, true);
+            for (int m = 0; m < P; ++m) v[0][m] = cscale(v[0][m], scale);
+        store_line<P, N / P>(v[0], data + field * N * nx + x, nx, t, true);
     }
 };
 
