@@ -88,13 +88,13 @@ int pss_grid::init()
         const double k = wavenumber(m, nx, p.lx);
         kx2v[m] = k * k;
         kxov[m] = (m == nx / 2) ? 0.0 : k;
-        kpx[m] = (3 * std::llabs(m < nx / 2 ? m : m - nx) < nx) ? 1.0 : 0.0;
+        kpx[m] = (!p.dealias || 3 * std::llabs(m < nx / 2 ? m : m - nx) < nx) ? 1.0 : 0.0;
     }
     for (int64_t m = 0; m < ny; ++m) {
         const double k = wavenumber(m, ny, p.ly);
         ky2v[m] = k * k;
         kyov[m] = (m == ny / 2) ? 0.0 : k;
-        kpy[m] = (3 * std::llabs(m < ny / 2 ? m : m - ny) < ny) ? 1.0 : 0.0;
+        kpy[m] = (!p.dealias || 3 * std::llabs(m < ny / 2 ? m : m - ny) < ny) ? 1.0 : 0.0;
     }
     if ((rc = upload((void **)&kx2d, kx2v.data(), nx * 8))) return rc;
     if ((rc = upload((void **)&ky2d, ky2v.data(), ny * 8))) return rc;
@@ -136,6 +136,13 @@ int pss_grid::init()
     owned_host.push_back(hp);
     host_sums = static_cast<double *>(hp);
     host_flags = reinterpret_cast<unsigned *>(static_cast<char *>(hp) + size_t(batch) * 3 * 8);
+    if (p.eq == PSS_EQ_NS) {
+        if ((rc = alloc(&ns_field, size_t(batch) * ns_field_bytes()))) return rc;
+        if ((rc = cuda(cudaMemset(ns_field, 0, size_t(batch) * ns_field_bytes()), "memset"))) return rc;
+        if ((rc = cuda(cudaMallocHost(&hp, size_t(batch) * ns_field_bytes()), "cudaMallocHost"))) return rc;
+        owned_host.push_back(hp);
+        host_fields = hp;
+    }
     return cuda(cudaDeviceSynchronize(), "init sync");
 }
 
@@ -185,9 +192,21 @@ int pss_grid::profile_resolve()
     return PSS_OK;
 }
 
+// per-field fixed-point record as written by the NS kernels
+struct NsFieldHost {
+    int idx, active, nonconv, pad;
+    long long updates;
+};
+
 int pss_grid::ns_update_count(int64_t *n)
 {
     *n = 0;
+    if (p.eq != PSS_EQ_NS || !has_state) return PSS_OK;
+    int rc = cuda(cudaMemcpyAsync(host_fields, ns_field, size_t(batch) * ns_field_bytes(), cudaMemcpyDeviceToHost,
+                                  stream), "fields copy");
+    if (rc || (rc = cuda(cudaStreamSynchronize(stream), "sync"))) return rc;
+    const NsFieldHost *f = static_cast<const NsFieldHost *>(host_fields);
+    for (int64_t i = 0; i < batch; ++i) *n += f[i].updates;
     return PSS_OK;
 }
 
@@ -286,16 +305,291 @@ template <class Rl> int nls_conserved(pss_grid *g, double *out)
 }  // namespace
 
 // ----------------------------------------------------------------------------
+// shared helpers
+
+namespace {
+
+// forward (-1) or inverse (+1, with 1/(nx ny)) 2D transform of buffer b
+template <class Rl> cudaError_t fft2(pss_grid *g, V2<Rl> *b, int dir)
+{
+    cudaError_t e = fft_rows<Rl>(b, g->nx, g->batch * g->ny, dir, Rl(1), Tw<Rl>(g->twx), g->stream);
+    if (e != cudaSuccess) return e;
+    const Rl sc = dir > 0 ? Rl(1.0 / (double(g->nx) * double(g->ny))) : Rl(1);
+    return fft_cols<Rl>(b, g->nx, g->ny, g->batch, dir, sc, Tw<Rl>(g->twy), g->stream);
+}
+
+// real caller array (host or device) -> complex buffer dst (imaginary part 0),
+// through the raw scratch buffer `tmp`
+template <class Rl> int load_real(pss_grid *g, const void *src, int where, int tmp, int dst, bool apply_sin)
+{
+    const size_t bytes = size_t(g->ntot) * sizeof(Rl);
+    int rc = g->cuda(cudaMemcpyAsync(g->buf[tmp], src, bytes, kind_in(where), g->stream), "state copy");
+    if (rc) return rc;
+    return g->cuda(real_to_complex<Rl>(static_cast<const Rl *>(g->buf[tmp]), B<Rl>(g, dst), g->ntot, apply_sin,
+                                       g->stream), "real to complex");
+}
+
+// Re(a - c b) of complex buffers into the caller array (through `tmp` for HOST)
+template <class Rl>
+int store_real(pss_grid *g, const V2<Rl> *a, const V2<Rl> *b, Rl c, void *dst, int where, int tmp)
+{
+    Rl *d = where == PSS_DEVICE ? static_cast<Rl *>(dst) : static_cast<Rl *>(g->buf[tmp]);
+    int rc = g->cuda(complex_to_real<Rl>(a, b, c, d, g->ntot, g->stream), "complex to real");
+    if (rc || where == PSS_DEVICE) return rc;
+    return g->cuda(cudaMemcpyAsync(dst, d, size_t(g->ntot) * sizeof(Rl), cudaMemcpyDeviceToHost, g->stream),
+                   "state copy");
+}
+
+template <class Rl> const Rl *Rt(const void *p) { return static_cast<const Rl *>(p); }
+
+int finish_sums(pss_grid *g)
+{
+    int rc = g->cuda(cudaMemcpyAsync(g->host_sums, g->sums, size_t(g->batch) * 3 * 8, cudaMemcpyDeviceToHost,
+                                     g->stream), "sums copy");
+    return rc ? rc : g->sync();
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// Sine-Gordon: buf[0] = uhat^n, buf[1] = d^n = uhat^n - uhat^{n-1},
+// buf[2] = H (column inverse transform of uhat^n / (nx ny)); buf[3], buf[4] scratch.
+
+namespace {
+
+// H from uhat: the same scaling-then-transform as the fused column pass
+template <class Rl> int sg_make_h(pss_grid *g)
+{
+    const Rl s = Rl(1.0 / (double(g->nx) * double(g->ny)));  // power of two: exact before or after
+    int rc = g->cuda(cudaMemcpyAsync(g->buf[2], g->buf[0], g->field_bytes(), cudaMemcpyDeviceToDevice, g->stream),
+                     "copy");
+    if (rc) return rc;
+    return g->cuda(fft_cols<Rl>(B<Rl>(g, 2), g->nx, g->ny, g->batch, +1, s, Tw<Rl>(g->twy), g->stream), "H");
+}
+
+template <class Rl> int sg_set(pss_grid *g, const void *u0, const void *v0, int where)
+{
+    int rc;
+    if ((rc = load_real<Rl>(g, u0, where, 3, 0, false))) return rc;
+    if ((rc = g->cuda(real_to_complex<Rl>(static_cast<const Rl *>(g->buf[3]), B<Rl>(g, 2), g->ntot, true, g->stream),
+                      "sin u0")))
+        return rc;
+    if (v0) {
+        if ((rc = load_real<Rl>(g, v0, where, 3, 1, false))) return rc;
+    } else if ((rc = g->cuda(cudaMemsetAsync(g->buf[1], 0, g->field_bytes(), g->stream), "memset"))) {
+        return rc;
+    }
+    for (int b : {0, 1, 2})
+        if ((rc = g->cuda(fft2<Rl>(g, B<Rl>(g, b), -1), "forward transform"))) return rc;
+    if ((rc = g->cuda(sg_init<Rl>(B<Rl>(g, 0), B<Rl>(g, 1), B<Rl>(g, 2), g->kx2d, g->ky2d, g->p.dt, g->nx, g->ny,
+                                  g->batch, g->stream), "sg init")))
+        return rc;
+    if ((rc = sg_make_h<Rl>(g))) return rc;
+    return where == PSS_HOST ? g->cuda(cudaStreamSynchronize(g->stream), "sync") : PSS_OK;
+}
+
+template <class Rl> int sg_step(pss_grid *g, int64_t n)
+{
+    int rc;
+    for (int64_t i = 0; i < n; ++i) {
+        if ((rc = g->pass_begin(0))) return rc;
+        cudaError_t e = sg_row_pass<Rl>(B<Rl>(g, 2), g->nx, g->batch * g->ny, Tw<Rl>(g->twx), g->stream);
+        if ((rc = g->pass_end()) || (rc = g->cuda(e, "sg row pass"))) return rc;
+        if ((rc = g->pass_begin(1))) return rc;
+        e = sg_col_pass<Rl>(B<Rl>(g, 2), B<Rl>(g, 0), B<Rl>(g, 1), g->nx, g->ny, g->batch, Rt<Rl>(g->kx2),
+                            Rt<Rl>(g->ky2), Rl(g->p.dt), Tw<Rl>(g->twy), g->stream);
+        if ((rc = g->pass_end()) || (rc = g->cuda(e, "sg column pass"))) return rc;
+    }
+    return PSS_OK;
+}
+
+// u^n -> a, u^{n-1} = Re F^-1 (uhat - d) -> b
+template <class Rl> int sg_get(pss_grid *g, void *a, void *b, int where)
+{
+    int rc;
+    if ((rc = g->cuda(cudaMemcpyAsync(g->buf[3], g->buf[0], g->field_bytes(), cudaMemcpyDeviceToDevice, g->stream),
+                      "copy")) ||
+        (rc = g->cuda(fft2<Rl>(g, B<Rl>(g, 3), +1), "inverse")) ||
+        (rc = store_real<Rl>(g, B<Rl>(g, 3), nullptr, Rl(0), a, where, 4)))
+        return rc;
+    if (b) {
+        if ((rc = g->cuda(cplx_axpy<Rl>(B<Rl>(g, 0), B<Rl>(g, 1), Rl(1), B<Rl>(g, 3), g->ntot, g->stream), "axpy")) ||
+            (rc = g->cuda(fft2<Rl>(g, B<Rl>(g, 3), +1), "inverse")) ||
+            (rc = store_real<Rl>(g, B<Rl>(g, 3), nullptr, Rl(0), b, where, 4)))
+            return rc;
+    }
+    return g->sync();
+}
+
+template <class Rl> int sg_conserved(pss_grid *g, double *out)
+{
+    int rc;
+    for (int k : {0, 1}) {
+        if ((rc = g->cuda(cudaMemcpyAsync(g->buf[3 + k], g->buf[k], g->field_bytes(), cudaMemcpyDeviceToDevice,
+                                          g->stream), "copy")) ||
+            (rc = g->cuda(fft2<Rl>(g, B<Rl>(g, 3 + k), +1), "inverse")))
+            return rc;
+    }
+    if ((rc = g->cuda(sg_sums<Rl>(B<Rl>(g, 3), B<Rl>(g, 4), B<Rl>(g, 0), B<Rl>(g, 1), g->nx, g->ny, g->batch, g->kx2d,
+                                  g->ky2d, g->p.dt, g->partials, g->sums, g->stream), "sg sums")) ||
+        (rc = finish_sums(g)))
+        return rc;
+    const double dA = g->dA(), inv_n = 1.0 / (double(g->nx) * double(g->ny));
+    bool finite = true;
+    for (int64_t f = 0; f < g->batch; ++f) {
+        const double *s = g->host_sums + 3 * f;
+        out[f] = dA * (s[0] + s[1]) + 0.5 * dA * s[2] * inv_n;
+        finite = finite && std::isfinite(out[f]);
+    }
+    return finite ? PSS_OK : g->fail(PSS_E_NONFINITE, "non-finite SG Hamiltonian");
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// Navier-Stokes: buf[0..2] vorticity iterates (per-field index in ns_field),
+// buf[3] = J_hat^n, buf[4] = C1, buf[5] = C2, buf[6] scratch.
+
+namespace {
+
+template <class Rl> void ns_w(pss_grid *g, V2<Rl> *w[3])
+{
+    for (int i = 0; i < 3; ++i) w[i] = B<Rl>(g, i);
+}
+
+template <class Rl> int ns_prep(pss_grid *g)
+{
+    return g->cuda(ns_prep_pass<Rl>(B<Rl>(g, 0), B<Rl>(g, 4), B<Rl>(g, 5), Rt<Rl>(g->kxo), Rt<Rl>(g->kyo),
+                                    Rt<Rl>(g->kx2), Rt<Rl>(g->ky2), g->nx, g->ny, g->batch, Tw<Rl>(g->twy),
+                                    g->stream), "ns derivatives");
+}
+
+template <class Rl> int ns_set(pss_grid *g, const void *w0, int where)
+{
+    int rc;
+    if ((rc = load_real<Rl>(g, w0, where, 6, 0, false)) || (rc = g->cuda(fft2<Rl>(g, B<Rl>(g, 0), -1), "forward")) ||
+        (rc = g->cuda(apply_mask<Rl>(B<Rl>(g, 0), Rt<Rl>(g->keepx), Rt<Rl>(g->keepy), g->nx, g->ny, g->batch, g->stream),
+                      "mask")) ||
+        (rc = g->cuda(cudaMemsetAsync(g->ns_field, 0, size_t(g->batch) * ns_field_bytes(), g->stream), "memset")) ||
+        (rc = ns_prep<Rl>(g)))
+        return rc;
+    return where == PSS_HOST ? g->cuda(cudaStreamSynchronize(g->stream), "sync") : PSS_OK;
+}
+
+template <class Rl> int ns_step(pss_grid *g, int64_t n)
+{
+    V2<Rl> *w[3];
+    ns_w<Rl>(g, w);
+    int *flag = reinterpret_cast<int *>(g->flags);
+    int *hflag = reinterpret_cast<int *>(g->host_flags);
+    const double parseval = g->p.lx * g->p.ly / (double(g->npts) * double(g->npts));
+    int rc;
+    for (int64_t s = 0; s < n; ++s) {
+        if ((rc = g->cuda(ns_begin(g->ns_field, g->batch, flag, g->stream), "ns begin"))) return rc;
+        for (int k = 0; k < g->p.max_iter; ++k) {
+            if ((rc = g->pass_begin(0))) return rc;
+            cudaError_t e = ns_row_pass<Rl>(B<Rl>(g, 4), B<Rl>(g, 5), g->ns_field, g->nx, g->ny, g->batch,
+                                            Tw<Rl>(g->twx), g->stream);
+            if ((rc = g->pass_end()) || (rc = g->cuda(e, "ns row pass"))) return rc;
+            int groups = 0;
+            if ((rc = g->pass_begin(1))) return rc;
+            e = ns_col_pass<Rl>(B<Rl>(g, 4), B<Rl>(g, 5), w, B<Rl>(g, 3), g->ns_field, g->partials, Rt<Rl>(g->kxo),
+                                Rt<Rl>(g->kyo), Rt<Rl>(g->kx2), Rt<Rl>(g->ky2), Rt<Rl>(g->keepx), Rt<Rl>(g->keepy),
+                                g->p.dt, g->p.nu, g->nx, g->ny, g->batch, k, Tw<Rl>(g->twy), &groups, g->stream);
+            if ((rc = g->pass_end()) || (rc = g->cuda(e, "ns column pass"))) return rc;
+            if ((rc = g->pass_begin(2))) return rc;
+            e = cudaMemsetAsync(flag, 0, sizeof(int), g->stream);
+            if (e == cudaSuccess)
+                e = ns_decide(g->ns_field, g->partials, groups, g->batch, k, parseval, g->p.tol, g->p.max_iter, flag,
+                              g->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, g->stream);
+            if ((rc = g->pass_end()) || (rc = g->cuda(e, "ns decide"))) return rc;
+            if ((rc = g->cuda(cudaStreamSynchronize(g->stream), "ns sync"))) return rc;
+            if (*hflag == 0) break;
+        }
+    }
+    // report fields that hit max_iter
+    if ((rc = g->cuda(cudaMemcpyAsync(g->host_fields, g->ns_field, size_t(g->batch) * ns_field_bytes(),
+                                      cudaMemcpyDeviceToHost, g->stream), "fields copy")) ||
+        (rc = g->cuda(cudaStreamSynchronize(g->stream), "sync")))
+        return rc;
+    const NsFieldHost *f = static_cast<const NsFieldHost *>(g->host_fields);
+    bool nc = false;
+    for (int64_t i = 0; i < g->batch; ++i) nc = nc || f[i].nonconv;
+    if (nc) {
+        // clear the sticky flags so that only new failures are reported later
+        if ((rc = g->cuda(cudaMemcpyAsync(g->host_fields, g->ns_field, size_t(g->batch) * ns_field_bytes(),
+                                          cudaMemcpyDeviceToHost, g->stream), "fields copy")))
+            return rc;
+        NsFieldHost *h = static_cast<NsFieldHost *>(g->host_fields);
+        for (int64_t i = 0; i < g->batch; ++i) h[i].nonconv = 0;
+        if ((rc = g->cuda(cudaMemcpyAsync(g->ns_field, h, size_t(g->batch) * ns_field_bytes(), cudaMemcpyHostToDevice,
+                                          g->stream), "fields copy")) ||
+            (rc = g->cuda(cudaStreamSynchronize(g->stream), "sync")))
+            return rc;
+        g->steps += n;
+        return g->fail(PSS_E_NOT_CONVERGED, "NS fixed point reached max_iter=%d", g->p.max_iter);
+    }
+    return PSS_OK;
+}
+
+// current vorticity of every field into buf[6]
+template <class Rl> int ns_current(pss_grid *g)
+{
+    V2<Rl> *w[3];
+    ns_w<Rl>(g, w);
+    return g->cuda(ns_gather<Rl>(g->ns_field, w, B<Rl>(g, 6), g->npts, g->batch, g->stream), "gather");
+}
+
+template <class Rl> int ns_get(pss_grid *g, void *a, int where)
+{
+    int rc;
+    if ((rc = ns_current<Rl>(g)) || (rc = g->cuda(fft2<Rl>(g, B<Rl>(g, 6), +1), "inverse")) ||
+        (rc = store_real<Rl>(g, B<Rl>(g, 6), nullptr, Rl(0), a, where, 3)))
+        return rc;
+    return g->sync();
+}
+
+template <class Rl> int ns_conserved(pss_grid *g, double *out)
+{
+    V2<Rl> *w[3];
+    ns_w<Rl>(g, w);
+    int rc;
+    if ((rc = g->cuda(ns_sums<Rl>(g->ns_field, w, g->nx, g->ny, g->batch, g->kx2d, g->ky2d, g->partials, g->sums,
+                                  g->stream), "ns sums")) ||
+        (rc = finish_sums(g)))
+        return rc;
+    const double dA = g->dA(), inv_n = 1.0 / (double(g->nx) * double(g->ny));
+    bool finite = true;
+    for (int64_t f = 0; f < g->batch; ++f) {
+        const double *s = g->host_sums + 3 * f;
+        out[3 * f] = dA * s[0];
+        out[3 * f + 1] = 0.5 * dA * s[1] * inv_n;
+        out[3 * f + 2] = 0.5 * dA * s[2] * inv_n;
+        for (int k = 0; k < 3; ++k) finite = finite && std::isfinite(out[3 * f + k]);
+    }
+    return finite ? PSS_OK : g->fail(PSS_E_NONFINITE, "non-finite NS invariant");
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
 // dispatch by equation and precision
+
+#define PSS_BY_PRECISION(CALL) (p.precision == PSS_FP32 ? CALL(float) : CALL(double))
 
 int pss_grid::set_state(const void *a, const void *b, int where)
 {
-    (void)b;
     steps = 0;
     nonconv_pending = false;
     int rc;
-    if (p.eq == PSS_EQ_NLS) rc = p.precision == PSS_FP32 ? nls_set<float>(this, a, where) : nls_set<double>(this, a, where);
-    else return fail(PSS_E_ARG, "equation %d not available", p.eq);
+#define NLS(R) nls_set<R>(this, a, where)
+#define SG(R) sg_set<R>(this, a, b, where)
+#define NS(R) ns_set<R>(this, a, where)
+    rc = p.eq == PSS_EQ_NLS ? PSS_BY_PRECISION(NLS) : p.eq == PSS_EQ_SG ? PSS_BY_PRECISION(SG) : PSS_BY_PRECISION(NS);
+#undef NLS
+#undef SG
+#undef NS
     if (!rc) has_state = true;
     return rc;
 }
@@ -304,49 +598,90 @@ int pss_grid::step_n(int64_t n)
 {
     if (n == 0) return PSS_OK;
     int rc;
-    if (p.eq == PSS_EQ_NLS) rc = p.precision == PSS_FP32 ? nls_step<float>(this, n) : nls_step<double>(this, n);
-    else return fail(PSS_E_ARG, "equation %d not available", p.eq);
+#define NLS(R) nls_step<R>(this, n)
+#define SG(R) sg_step<R>(this, n)
+#define NS(R) ns_step<R>(this, n)
+    rc = p.eq == PSS_EQ_NLS ? PSS_BY_PRECISION(NLS) : p.eq == PSS_EQ_SG ? PSS_BY_PRECISION(SG) : PSS_BY_PRECISION(NS);
+#undef NLS
+#undef SG
+#undef NS
     if (!rc) steps += n;
     return rc;
 }
 
 int pss_grid::get_state(void *a, void *b, int where)
 {
-    (void)b;
-    if (p.eq == PSS_EQ_NLS) return p.precision == PSS_FP32 ? nls_get<float>(this, a, where) : nls_get<double>(this, a, where);
-    return fail(PSS_E_ARG, "equation %d not available", p.eq);
+#define NLS(R) nls_get<R>(this, a, where)
+#define SG(R) sg_get<R>(this, a, b, where)
+#define NS(R) ns_get<R>(this, a, where)
+    return p.eq == PSS_EQ_NLS ? PSS_BY_PRECISION(NLS) : p.eq == PSS_EQ_SG ? PSS_BY_PRECISION(SG) : PSS_BY_PRECISION(NS);
+#undef NLS
+#undef SG
+#undef NS
 }
 
 int pss_grid::conserved(double *out)
 {
-    if (p.eq == PSS_EQ_NLS) return p.precision == PSS_FP32 ? nls_conserved<float>(this, out) : nls_conserved<double>(this, out);
-    return fail(PSS_E_ARG, "equation %d not available", p.eq);
+#define NLS(R) nls_conserved<R>(this, out)
+#define SG(R) sg_conserved<R>(this, out)
+#define NS(R) ns_conserved<R>(this, out)
+    return p.eq == PSS_EQ_NLS ? PSS_BY_PRECISION(NLS) : p.eq == PSS_EQ_SG ? PSS_BY_PRECISION(SG) : PSS_BY_PRECISION(NS);
+#undef NLS
+#undef SG
+#undef NS
 }
 
+// Checkpoint layout: the exact state buffers (NLS: row transform of psi;
+// SG: uhat^n, d^n; NS: w_hat^n of every field), then {steps, NS updates}.
 size_t pss_grid::checkpoint_bytes() const
 {
     const int nstate = p.eq == PSS_EQ_SG ? 2 : 1;
     return size_t(nstate) * size_t(ntot) * esz + 16;
 }
 
-int pss_grid::checkpoint(void *buf, int where, bool save)
+int pss_grid::checkpoint(void *buf_, int where, bool save)
 {
     const int nstate = p.eq == PSS_EQ_SG ? 2 : 1;
-    char *b = static_cast<char *>(buf);
+    char *b = static_cast<char *>(buf_);
     int rc;
+    int src_of[2] = {0, 1};
+    if (save && p.eq == PSS_EQ_NS) {
+        rc = p.precision == PSS_FP32 ? ns_current<float>(this) : ns_current<double>(this);
+        if (rc) return rc;
+        src_of[0] = 6;
+    }
     for (int i = 0; i < nstate; ++i) {
-        if (save) rc = cuda(cudaMemcpyAsync(b + i * field_bytes(), this->buf[i], field_bytes(), kind_out(where), stream), "checkpoint");
-        else rc = cuda(cudaMemcpyAsync(this->buf[i], b + i * field_bytes(), field_bytes(), kind_in(where), stream), "checkpoint");
+        if (save)
+            rc = cuda(cudaMemcpyAsync(b + i * field_bytes(), this->buf[src_of[i]], field_bytes(), kind_out(where), stream),
+                      "checkpoint");
+        else
+            rc = cuda(cudaMemcpyAsync(this->buf[i], b + i * field_bytes(), field_bytes(), kind_in(where), stream),
+                      "checkpoint");
         if (rc) return rc;
     }
     int64_t meta[2] = {steps, 0};
+    if (save && (rc = ns_update_count(&meta[1]))) return rc;
     char *mb = b + nstate * field_bytes();
-    if (save) rc = cuda(cudaMemcpyAsync(mb, meta, 16, where == PSS_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice, stream), "checkpoint meta");
-    else rc = cuda(cudaMemcpyAsync(meta, mb, 16, where == PSS_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost, stream), "checkpoint meta");
-    if (rc) return rc;
-    if ((rc = cuda(cudaStreamSynchronize(stream), "checkpoint sync"))) return rc;
+    if (save)
+        rc = cuda(cudaMemcpyAsync(mb, meta, 16, where == PSS_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice, stream),
+                  "checkpoint meta");
+    else
+        rc = cuda(cudaMemcpyAsync(meta, mb, 16, where == PSS_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost, stream),
+                  "checkpoint meta");
+    if (rc || (rc = cuda(cudaStreamSynchronize(stream), "checkpoint sync"))) return rc;
     if (!save) {
         steps = meta[0];
+        if (p.eq == PSS_EQ_SG) {
+            rc = p.precision == PSS_FP32 ? sg_make_h<float>(this) : sg_make_h<double>(this);
+        } else if (p.eq == PSS_EQ_NS) {
+            // all fields restart from buffer 0 with their update count
+            NsFieldHost *h = static_cast<NsFieldHost *>(host_fields);
+            for (int64_t i = 0; i < batch; ++i) h[i] = NsFieldHost{0, 0, 0, 0, i == 0 ? meta[1] : 0};
+            rc = cuda(cudaMemcpyAsync(ns_field, h, size_t(batch) * ns_field_bytes(), cudaMemcpyHostToDevice, stream),
+                      "fields");
+            if (!rc) rc = p.precision == PSS_FP32 ? ns_prep<float>(this) : ns_prep<double>(this);
+        }
+        if (rc || (rc = cuda(cudaStreamSynchronize(stream), "restore sync"))) return rc;
         has_state = true;
     }
     return PSS_OK;

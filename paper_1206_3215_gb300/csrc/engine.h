@@ -41,8 +41,8 @@ struct pss_grid {
     unsigned *host_flags = nullptr;
 
     // NS fixed-point bookkeeping (device, per field)
-    void *ns_field = nullptr;
-    int *host_active = nullptr;
+    void *ns_field = nullptr;     // device, batch records (see k_ns.cu)
+    void *host_fields = nullptr;  // pinned copy of the records
 
     // tracing: event pairs around passes (kind 0 row, 1 column, 2 other)
     bool profiling = false;

@@ -41,6 +41,49 @@ template <class Rl>
 cudaError_t nls_col_pass(V2<Rl> *data, int64_t nx, int64_t ny, int64_t batch, Rl scale,
                          const TW<Rl> *ax, const TW<Rl> *by, const TW<Rl> *twy, cudaStream_t s);
 
+// ---- sine-Gordon passes (k_sg.cu) ---------------------------------------------
+// Row pass on H (column inverse transform of uhat^n / (nx ny)): row inverse
+// FFT, s = sin(Re), row forward FFT, in place.
+template <class Rl>
+cudaError_t sg_row_pass(V2<Rl> *h, int64_t nx, int64_t rows_total, const TW<Rl> *twx, cudaStream_t s);
+// Column pass: column FFT of S = F sin u^n; d <- d - (a u + dt^2 S)/(1 + a/4),
+// u <- u + d (a = dt^2 |k|^2), in place; H <- column inverse FFT of u / (nx ny).
+template <class Rl>
+cudaError_t sg_col_pass(V2<Rl> *h, V2<Rl> *u, V2<Rl> *d, int64_t nx, int64_t ny, int64_t batch,
+                        const Rl *kx2, const Rl *ky2, Rl dt, const TW<Rl> *twy, cudaStream_t s);
+
+// ---- Navier-Stokes passes (k_ns.cu) -------------------------------------------
+size_t ns_field_bytes();  // bytes of the per-field fixed-point record
+template <class Rl>
+cudaError_t ns_row_pass(V2<Rl> *c1, V2<Rl> *c2, const void *fs, int64_t nx, int64_t ny, int64_t batch,
+                        const TW<Rl> *twx, cudaStream_t s);
+template <class Rl>
+cudaError_t ns_col_pass(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, void *fs, double *partials,
+                        const Rl *kxo, const Rl *kyo, const Rl *kx2, const Rl *ky2, const Rl *keepx,
+                        const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch, int k,
+                        const TW<Rl> *twy, int *groups_out, cudaStream_t s);
+template <class Rl>
+cudaError_t ns_prep_pass(const V2<Rl> *w, V2<Rl> *c1, V2<Rl> *c2, const Rl *kxo, const Rl *kyo,
+                         const Rl *kx2, const Rl *ky2, int64_t nx, int64_t ny, int64_t batch,
+                         const TW<Rl> *twy, cudaStream_t s);
+cudaError_t ns_begin(void *fs, int64_t batch, int *any_active, cudaStream_t s);
+cudaError_t ns_decide(void *fs, const double *partials, int64_t groups, int64_t batch, int k, double parseval,
+                      double tol, int max_iter, int *any_active, cudaStream_t s);
+
+// ---- elementwise helpers (k_util.cu) ----------------------------------------
+template <class Rl> cudaError_t real_to_complex(const Rl *src, V2<Rl> *dst, int64_t n, bool apply_sin, cudaStream_t s);
+template <class Rl>
+cudaError_t complex_to_real(const V2<Rl> *a, const V2<Rl> *b, Rl c, Rl *dst, int64_t n, cudaStream_t s);
+template <class Rl>
+cudaError_t sg_init(const V2<Rl> *u, V2<Rl> *d, const V2<Rl> *sn, const double *kx2, const double *ky2, double dt,
+                    int64_t nx, int64_t ny, int64_t batch, cudaStream_t s);
+template <class Rl>
+cudaError_t ns_gather(const void *fs, V2<Rl> *const w[3], V2<Rl> *dst, int64_t per_field, int64_t batch,
+                      cudaStream_t s);
+template <class Rl> cudaError_t cplx_axpy(const V2<Rl> *a, const V2<Rl> *b, Rl c, V2<Rl> *dst, int64_t n, cudaStream_t s);
+template <class Rl>
+cudaError_t apply_mask(V2<Rl> *a, const Rl *keepx, const Rl *keepy, int64_t nx, int64_t ny, int64_t batch, cudaStream_t s);
+
 // ---- deterministic FP64 reductions (k_reduce.cu) -----------------------------
 constexpr int RED_BLOCKS = 128;  // partial sums per field
 constexpr int RED_THREADS = 256;
@@ -54,6 +97,16 @@ cudaError_t nls_sums(const V2<Rl> *psi, const V2<Rl> *psi_hat, int64_t nx, int64
 
 // message returned by pss_last_error(NULL) for calls without a grid handle
 void set_global_error(const char *msg);
+
+// SG: per field {sum (Y/dt)^2/2, sum 1 - cos(X - Y/2), sum |k|^2 |U - D/2|^2}
+template <class Rl>
+cudaError_t sg_sums(const V2<Rl> *X, const V2<Rl> *Y, const V2<Rl> *U, const V2<Rl> *D, int64_t nx, int64_t ny,
+                    int64_t batch, const double *kx2, const double *ky2, double dt, double *partials, double *out,
+                    cudaStream_t s);
+// NS: per field {Re w_hat(0,0), sum |w_hat|^2, sum_{k != 0} |w_hat|^2 / |k|^2}
+template <class Rl>
+cudaError_t ns_sums(const void *fs, V2<Rl> *const w[3], int64_t nx, int64_t ny, int64_t batch, const double *kx2,
+                    const double *ky2, double *partials, double *out, cudaStream_t s);
 
 // status bits written by reductions
 constexpr unsigned FLAG_NONFINITE = 1u;

@@ -83,6 +83,96 @@ cudaError_t nls_sums(const V2<Rl> *psi, const V2<Rl> *psi_hat, int64_t nx, int64
     return cudaGetLastError();
 }
 
+// SG at t_{n-1/2}: X = u^n, Y = u^n - u^{n-1} (physical, real parts), U = uhat^n,
+// D = uhat^n - uhat^{n-1}.  Sums: (Y/dt)^2 / 2, 1 - cos(ubar) = 2 sin^2(ubar/2)
+// with ubar = X - Y/2, and |k|^2 |U - D/2|^2 (the spectrum of ubar).
+template <class Rl>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_sg_sums(const V2<Rl> *X, const V2<Rl> *Y, const V2<Rl> *U, const V2<Rl> *D, int64_t nx, int64_t ny,
+              const double *kx2, const double *ky2, double dt, double *partials)
+{
+    __shared__ double sh[3 * RED_THREADS];
+    const int64_t f = blockIdx.y, n = nx * ny, o = f * n;
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = int64_t(blockIdx.x) * RED_THREADS + threadIdx.x; i < n;
+         i += int64_t(RED_BLOCKS) * RED_THREADS) {
+        const double du = double(Y[o + i].x), ub = double(X[o + i].x) - 0.5 * du;
+        const double sh2 = sin(0.5 * ub);
+        a[0] += 0.5 * (du / dt) * (du / dt);
+        a[1] += 2.0 * sh2 * sh2;
+        const V2<Rl> u = U[o + i], d = D[o + i];
+        const double br = double(u.x) - 0.5 * double(d.x), bi = double(u.y) - 0.5 * double(d.y);
+        a[2] += (kx2[i % nx] + ky2[i / nx]) * (br * br + bi * bi);
+    }
+    block_sum<3>(a, sh);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) partials[(f * RED_BLOCKS + blockIdx.x) * 3 + k] = a[k];
+}
+
+// NS from the spectrum w_hat of each field (buffer fs[f].idx): Re w_hat(0,0)
+// (= sum of w), sum |w_hat|^2, sum over k != 0 of |w_hat|^2 / |k|^2.
+struct NsFieldRd {
+    int idx, active, nonconv, pad;
+    long long updates;
+};
+template <class Rl>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_ns_sums(const NsFieldRd *fs, const V2<Rl> *w0, const V2<Rl> *w1, const V2<Rl> *w2, int64_t nx, int64_t ny,
+              const double *kx2, const double *ky2, double *partials)
+{
+    __shared__ double sh[3 * RED_THREADS];
+    const int64_t f = blockIdx.y, n = nx * ny;
+    const int b = fs[f].idx;
+    const V2<Rl> *w = (b == 0 ? w0 : b == 1 ? w1 : w2) + f * n;
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = int64_t(blockIdx.x) * RED_THREADS + threadIdx.x; i < n;
+         i += int64_t(RED_BLOCKS) * RED_THREADS) {
+        const V2<Rl> z = w[i];
+        const double m2 = double(z.x) * z.x + double(z.y) * z.y;
+        const double k2 = kx2[i % nx] + ky2[i / nx];
+        if (i == 0) a[0] += double(z.x);
+        a[1] += m2;
+        if (k2 > 0) a[2] += m2 / k2;
+    }
+    block_sum<3>(a, sh);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) partials[(f * RED_BLOCKS + blockIdx.x) * 3 + k] = a[k];
+}
+
+template <class Rl>
+cudaError_t sg_sums(const V2<Rl> *X, const V2<Rl> *Y, const V2<Rl> *U, const V2<Rl> *D, int64_t nx, int64_t ny,
+                    int64_t batch, const double *kx2, const double *ky2, double dt, double *partials, double *out,
+                    cudaStream_t s)
+{
+    k_sg_sums<Rl><<<dim3(RED_BLOCKS, unsigned(batch)), RED_THREADS, 0, s>>>(X, Y, U, D, nx, ny, kx2, ky2, dt,
+                                                                           partials);
+    k_fold<3><<<unsigned(batch), RED_THREADS, 0, s>>>(partials, out);
+    return cudaGetLastError();
+}
+
+template <class Rl>
+cudaError_t ns_sums(const void *fs, V2<Rl> *const w[3], int64_t nx, int64_t ny, int64_t batch, const double *kx2,
+                    const double *ky2, double *partials, double *out, cudaStream_t s)
+{
+    k_ns_sums<Rl><<<dim3(RED_BLOCKS, unsigned(batch)), RED_THREADS, 0, s>>>(
+        static_cast<const NsFieldRd *>(fs), w[0], w[1], w[2], nx, ny, kx2, ky2, partials);
+    k_fold<3><<<unsigned(batch), RED_THREADS, 0, s>>>(partials, out);
+    return cudaGetLastError();
+}
+
+template cudaError_t sg_sums<float>(const float2 *, const float2 *, const float2 *, const float2 *, int64_t,
+                                    int64_t, int64_t, const double *, const double *, double, double *, double *,
+                                    cudaStream_t);
+template cudaError_t sg_sums<double>(const double2 *, const double2 *, const double2 *, const double2 *, int64_t,
+                                     int64_t, int64_t, const double *, const double *, double, double *,
+                                     double *, cudaStream_t);
+template cudaError_t ns_sums<float>(const void *, float2 *const[3], int64_t, int64_t, int64_t, const double *,
+                                    const double *, double *, double *, cudaStream_t);
+template cudaError_t ns_sums<double>(const void *, double2 *const[3], int64_t, int64_t, int64_t, const double *,
+                                     const double *, double *, double *, cudaStream_t);
+
 template cudaError_t nls_sums<float>(const float2 *, const float2 *, int64_t, int64_t, int64_t,
                                      const double *, const double *, double *, double *,
                                      cudaStream_t);

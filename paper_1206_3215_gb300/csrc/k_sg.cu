@@ -1,0 +1,104 @@
+// Fused passes of the sine-Gordon semi-implicit leapfrog (Eq. 3, Section 4.2).
+//
+// The scheme (u^{n+1} - 2u^n + u^{n-1})/dt^2 - Lap (u^{n+1} + 2u^n + u^{n-1})/4
+// = -sin u^n is solved in Fourier space.  The two time levels are held as
+// uhat^n and the increment d^n = uhat^n - uhat^{n-1}; with a = dt^2 |k|^2 the
+// recurrence
+//   uhat^{n+1} = [(2 - a/2) uhat^n - dt^2 F sin u^n] / (1 + a/4) - uhat^{n-1}
+// is, identically,
+//   d^{n+1} = d^n - (a uhat^n + dt^2 F sin u^n) / (1 + a/4),
+//   uhat^{n+1} = uhat^n + d^{n+1},
+// which forms the small increment directly instead of the difference of two
+// nearly equal levels (the cancellation would otherwise cost FP32 most of
+// its digits at dt = 1e-3).
+//
+// State between passes: H = column inverse transform of uhat^n / (nx ny)
+// (x in Fourier space, y physical).  A row pass turns H into u^n, takes
+// sin u^n and transforms the row forward (S).  A column pass transforms S
+// forward (F sin u^n), updates uhat and d in place, and writes the column
+// inverse transform of the new uhat as the next H.
+#include "launch.cuh"
+
+namespace pss {
+
+__device__ __forceinline__ float sin_(float a) { return sinf(a); }
+__device__ __forceinline__ double sin_(double a) { return sin(a); }
+
+template <class Rl> struct SgRow {
+    static constexpr int NIN = 1;
+    V2<Rl> *h;  // in: H rows; out: S rows (in place)
+    __device__ const V2<Rl> *in(int) const { return h; }
+    template <int N, int P, bool BLOCK, class Sm>
+    __device__ __forceinline__ void row(V2<Rl> (&vv)[1][P], int64_t r, bool ok, int t, const Sm (&sm)[1],
+                                        const TW<Rl> *tw) const
+    {
+        V2<Rl>(&v)[P] = vv[0];
+        block_fft<N, P, +1, BLOCK>(v, sm[0], t, tw);
+        fence(v);
+#pragma unroll
+        for (int m = 0; m < P; ++m) v[m] = V2<Rl>{sin_(v[m].x), Rl(0)};
+        fence(v);
+        block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw);
+        store_line<P, N / P>(v, h + r * N, 1, t, ok);
+    }
+};
+
+template <class Rl> struct SgCol {
+    static constexpr int NIN = 1;
+    V2<Rl> *h;          // in: S columns; out: next H
+    V2<Rl> *u, *d;      // uhat^n, d^n, updated in place
+    const Rl *kx2, *ky2;
+    Rl dt2, inv_n2;     // dt^2, 1/(nx ny)
+    int64_t nx;
+    __device__ const V2<Rl> *in(int) const { return h; }
+    template <int N, int P, bool BLOCK, class Sm>
+    __device__ __forceinline__ void col(V2<Rl> (&vv)[1][P], int64_t field, int x, int t,
+                                        const Sm (&sm)[1], const TW<Rl> *tw) const
+    {
+        constexpr int T = N / P;
+        V2<Rl>(&v)[P] = vv[0];
+        const int64_t base = field * N * nx + x;
+        block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw);
+        fence(v);
+        const Rl kx = __ldg(kx2 + x);
+#pragma unroll
+        for (int m = 0; m < P; ++m) {
+            const int y = t + T * m;
+            const int64_t i = base + int64_t(y) * nx;
+            const V2<Rl> un = u[i], dn = d[i];
+            const Rl a = dt2 * (kx + __ldg(ky2 + y));
+            const Rl inv = Rl(1) / (Rl(1) + Rl(0.25) * a);
+            const V2<Rl> dn1{dn.x - (a * un.x + dt2 * v[m].x) * inv, dn.y - (a * un.y + dt2 * v[m].y) * inv};
+            const V2<Rl> un1{un.x + dn1.x, un.y + dn1.y};
+            d[i] = dn1;
+            u[i] = un1;
+            v[m] = cscale(un1, inv_n2);
+        }
+        fence(v);
+        block_fft<N, P, +1, BLOCK>(v, sm[0], t, tw);
+        store_line<P, T>(v, h + base, nx, t, true);
+    }
+};
+
+template <class Rl>
+cudaError_t sg_row_pass(V2<Rl> *h, int64_t nx, int64_t rows_total, const TW<Rl> *twx, cudaStream_t s)
+{
+    return launch_row<Rl>(nx, SgRow<Rl>{h}, twx, rows_total, s);
+}
+
+template <class Rl>
+cudaError_t sg_col_pass(V2<Rl> *h, V2<Rl> *u, V2<Rl> *d, int64_t nx, int64_t ny, int64_t batch,
+                        const Rl *kx2, const Rl *ky2, Rl dt, const TW<Rl> *twy, cudaStream_t s)
+{
+    SgCol<Rl> op{h, u, d, kx2, ky2, dt * dt, Rl(1.0 / (double(nx) * double(ny))), nx};
+    return launch_col<Rl>(ny, nx, op, twy, batch, s);
+}
+
+#define PSS_INST(Rl)                                                                              \
+    template cudaError_t sg_row_pass<Rl>(V2<Rl> *, int64_t, int64_t, const TW<Rl> *, cudaStream_t); \
+    template cudaError_t sg_col_pass<Rl>(V2<Rl> *, V2<Rl> *, V2<Rl> *, int64_t, int64_t, int64_t,   \
+                                         const Rl *, const Rl *, Rl, const TW<Rl> *, cudaStream_t);
+PSS_INST(float)
+PSS_INST(double)
+
+}  // namespace pss

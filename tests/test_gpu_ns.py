@@ -1,0 +1,142 @@
+"""Parity of the Navier-Stokes Crank-Nicolson / fixed-point path (Section
+4.3) through the C ABI against the FP64 oracle, Table 4's Taylor-Green error
+and closed forms."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synthetic as S
+from gpu_util import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+
+
+def _golden(name):
+    vals = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", name)):
+        line = line.split("#")[0].split()
+        if len(line) == 2:
+            vals[line[0]] = float(line[1])
+    return vals
+
+
+def _cn_error(amp, lam, nu, dt, steps):
+    a = nu * lam * dt
+    g = (1 - a / 2) / (1 + a / 2)
+    return amp * abs(g ** steps - math.exp(-a * steps))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [64, 256])
+def test_taylor_green_table4(lib, cuda_device, precision, n):
+    g0 = _golden("ns_taylor_green_table4.txt")
+    steps, dt, nu = int(g0["steps"]), g0["dt"], g0["nu"]
+    g = lib.Grid("ns", n, precision, lx=1.0, ly=1.0, dt=dt, nu=nu, tol=g0["tol"], dealias=0)
+    g.set_state(S.taylor_green_paper(n)[None])
+    g.step(steps)
+    w = g.get_state()[0]
+    err = np.abs(w - S.taylor_green_paper(n, t=steps * dt, nu=nu)).max()
+    exact_err = _cn_error(4 * math.pi, 8 * math.pi ** 2, nu, dt, steps)
+    if precision == "fp64":
+        assert abs(err - exact_err) <= 1e-10
+        assert round(err, 7) == pytest.approx(g0["max_error"], abs=5e-8)
+    else:
+        # FP32: one ulp of a field of amplitude 4 pi is ~1e-6; 20 steps of
+        # unbiased rounding stay within 1e-5
+        assert abs(err - exact_err) <= 1e-5
+    steps_done, updates = g.stats()
+    assert steps_done == steps and updates == 2 * steps  # J = 0: two updates per step
+
+
+def test_taylor_green_2pi_box_256(lib, cuda_device):
+    n, nu, dt, steps = 256, 1e-3, 2.5e-4, 40
+    g = lib.Grid("ns", n, "fp64", lx=2 * math.pi, ly=2 * math.pi, dt=dt, nu=nu, dealias=1)
+    g.set_state(S.taylor_green_2pi(n)[None])
+    g.step(steps)
+    err = np.abs(g.get_state()[0] - S.taylor_green_2pi(n, t=steps * dt, nu=nu)).max()
+    assert abs(err - _cn_error(2.0, 2.0, nu, dt, steps)) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [64, 128])
+def test_random_field_matches_oracle(lib, orc, cuda_device, precision, n):
+    L, nu, dt, steps = 2 * math.pi, 1e-3, 2.5e-3, 20
+    w0 = S.ns_power_law(n)
+    ref, iters, ok = orc.ns_run(orc.ns_init(w0, True), L, L, nu, dt, steps)
+    assert ok
+    g = lib.Grid("ns", n, precision, lx=L, ly=L, dt=dt, nu=nu, tol=1e-10, dealias=1)
+    g.set_state(w0[None])
+    g.step(steps)
+    got = g.get_state()[0]
+    err = rel_l2(got, orc.ns_field(ref))
+    assert err <= (TOL64 if precision == "fp64" else 1e-5), err
+    if precision == "fp64":
+        assert g.stats()[1] == int(iters.sum())
+    c0, z0, e0 = orc.ns_invariants(ref, L, L)
+    (c, z, e), = g.conserved()
+    assert abs(z - z0) / z0 <= (1e-10 if precision == "fp64" else 1e-5)
+    assert abs(e - e0) / e0 <= (1e-10 if precision == "fp64" else 1e-5)
+
+
+def test_fields_converging_differently_match_alone(lib, cuda_device):
+    # a Taylor-Green field (J = 0: 2 updates per step) and a random field
+    # (more updates) in one batch: each equals its solo run bit for bit
+    n, L, nu, dt = 64, 2 * math.pi, 1e-3, 2.5e-3
+    fields = np.stack([S.taylor_green_2pi(n), S.ns_power_law(n)])
+    g = lib.Grid("ns", n, "fp32", batch=2, lx=L, ly=L, dt=dt, nu=nu)
+    g.set_state(fields)
+    g.step(5)
+    together = g.get_state()
+    total = g.stats()[1]
+    solo_updates = 0
+    for i in range(2):
+        h = lib.Grid("ns", n, "fp32", lx=L, ly=L, dt=dt, nu=nu)
+        h.set_state(fields[i:i + 1])
+        h.step(5)
+        assert np.array_equal(h.get_state()[0], together[i])
+        solo_updates += h.stats()[1]
+    assert total == solo_updates
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_checkpoint_resume_is_bitwise(lib, cuda_device, precision):
+    n, L, nu, dt = 64, 2 * math.pi, 1e-3, 2.5e-3
+    w0 = S.ns_power_law(n)[None]
+    a = lib.Grid("ns", n, precision, lx=L, ly=L, dt=dt, nu=nu)
+    a.set_state(w0)
+    a.step(4)
+    ck = a.checkpoint()
+    a.step(4)
+    b = lib.Grid("ns", n, precision, lx=L, ly=L, dt=dt, nu=nu)
+    b.restore(ck)
+    b.step(4)
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert a.stats() == b.stats()
+
+
+def test_non_convergence_is_reported_and_handle_stays_usable(lib, cuda_device):
+    n, L = 32, 2 * math.pi
+    g = lib.Grid("ns", n, "fp64", lx=L, ly=L, dt=2.5e-3, nu=1e-3, max_iter=1)
+    g.set_state(S.ns_power_law(n)[None])
+    with pytest.raises(lib.PssError) as e:
+        g.step(3)
+    assert e.value.code == lib.PSS_E_NOT_CONVERGED
+    assert np.isfinite(g.get_state()).all()
+    assert g.stats()[1] == 3
+
+
+def test_circulation_is_conserved_at_config4_size(lib, cuda_device):
+    # 4096^2 FP32, the Navier-Stokes workload's grid: the mean vorticity is
+    # conserved exactly by the scheme (J_hat(0) = 0); enstrophy only decays
+    n, L = 4096, 2 * math.pi
+    g = lib.Grid("ns", n, "fp32", lx=L, ly=L, dt=2.5e-4, nu=1e-3)
+    g.set_state(S.ns_power_law(n)[None])
+    (c0, z0, e0), = g.conserved()
+    g.step(3)
+    (c1, z1, e1), = g.conserved()
+    assert abs(c1 - c0) <= 1e-9 * math.sqrt(z0) * L
+    assert z1 <= z0 * (1 + 1e-6) and e1 <= e0 * (1 + 1e-6)

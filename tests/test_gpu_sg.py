@@ -1,0 +1,119 @@
+"""Parity of the sine-Gordon leapfrog (Eq. 3, Section 4.2) through the C ABI
+against the FP64 oracle and the scheme's closed forms."""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as S
+from gpu_util import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+L = 10 * math.pi
+TOL64 = 1e-10
+# FP32: relative L2 of u after the run; derived from ~1e-7 per pass rounding
+# accumulated as a random walk over the steps (measured and stated in the design notes)
+TOL32 = 2e-5
+
+
+def _grid(lib, n, precision, batch=1, dt=1e-3):
+    return lib.Grid("sg", n, precision, batch=batch, lx=L, ly=L, x0=-L / 2, y0=-L / 2, dt=dt)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,steps", [(64, 200), (256, 100)])
+def test_gaussian_matches_oracle(lib, orc, cuda_device, precision, n, steps):
+    dt = 1e-3
+    u0, v0 = S.sg_gaussian(n)
+    un, um = orc.sg_init(u0, v0, L, L, dt)
+    un, um = orc.sg_run(un, um, L, L, dt, steps)
+    ref_n, ref_m = orc.sg_fields(un, um)
+    g = _grid(lib, n, precision, dt=dt)
+    g.set_state(u0[None], v0[None])
+    g.step(steps)
+    a, b = g.get_state()
+    tol = TOL64 if precision == "fp64" else TOL32
+    assert rel_l2(a[0], ref_n) <= tol
+    assert rel_l2(b[0], ref_m) <= tol
+    # the increment u^n - u^{n-1} carries the velocity: compare it too
+    assert rel_l2(a[0] - b[0], ref_n - ref_m) <= (1e-8 if precision == "fp64" else 2e-3)
+
+
+def test_uniform_field_is_the_pendulum(lib, cuda_device):
+    n, dt, steps, u0, v0 = 16, 1e-2, 300, 0.9, 0.3
+    g = _grid(lib, n, "fp64", dt=dt)
+    g.set_state(np.full((1, n, n), u0), np.full((1, n, n), v0))
+    g.step(steps)
+    a, b = g.get_state()
+    u, up = u0, u0 - dt * v0 - 0.5 * dt * dt * math.sin(u0)
+    for _ in range(steps):
+        u, up = 2 * u - up - dt * dt * math.sin(u), u
+    assert np.abs(a - u).max() <= 1e-12 and np.abs(b - up).max() <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_hamiltonian_matches_oracle_and_is_conserved(lib, orc, cuda_device, precision):
+    n, dt, steps = 128, 1e-3, 500
+    u0, v0 = S.sg_gaussian(n)
+    un, um = orc.sg_init(u0, v0, L, L, dt)
+    H0 = orc.sg_hamiltonian(un, um, L, L, dt)
+    g = _grid(lib, n, precision, dt=dt)
+    g.set_state(u0[None], v0[None])
+    (h0,), = g.conserved()
+    assert abs(h0 - H0) / H0 <= (1e-12 if precision == "fp64" else 1e-5)
+    g.step(steps)
+    (h1,), = g.conserved()
+    # Section 5.2: the final Hamiltonian within 6 significant figures
+    assert abs(h1 - h0) / h0 <= (1e-6 if precision == "fp64" else 1e-5)
+
+
+def test_batch_is_bitwise_equal_to_alone(lib, cuda_device):
+    n = 64
+    u0, v0 = S.sg_gaussian(n, batch=3)
+    g = _grid(lib, n, "fp32", batch=3)
+    g.set_state(u0, v0)
+    g.step(40)
+    a, b = g.get_state()
+    for i in range(3):
+        h = _grid(lib, n, "fp32")
+        h.set_state(u0[i:i + 1], v0[i:i + 1])
+        h.step(40)
+        a1, b1 = h.get_state()
+        assert np.array_equal(a1[0], a[i]) and np.array_equal(b1[0], b[i])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_checkpoint_resume_is_bitwise(lib, cuda_device, precision):
+    n = 128
+    u0, v0 = S.sg_gaussian(n)
+    a = _grid(lib, n, precision)
+    a.set_state(u0[None], v0[None])
+    a.step(25)
+    ck = a.checkpoint()
+    a.step(25)
+    b = _grid(lib, n, precision)
+    b.restore(ck)
+    b.step(25)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+
+
+def test_config3_size_matches_oracle_over_100_steps(lib, orc, cuda_device):
+    # 2048^2 (the sine-Gordon workload's grid), FP64 GPU path against the
+    # oracle for 100 steps; the FP32 path against the FP64 GPU path
+    n, dt, steps = 2048, 1e-3, 100
+    u0, v0 = S.sg_gaussian(n)
+    un, um = orc.sg_init(u0, v0, L, L, dt)
+    un, um = orc.sg_run(un, um, L, L, dt, steps)
+    ref_n, _ = orc.sg_fields(un, um)
+    g = _grid(lib, n, "fp64", dt=dt)
+    g.set_state(u0[None], v0[None])
+    g.step(steps)
+    a64, _ = g.get_state()
+    assert rel_l2(a64[0], ref_n) <= TOL64
+    g32 = _grid(lib, n, "fp32", dt=dt)
+    g32.set_state(u0[None], v0[None])
+    g32.step(steps)
+    a32, _ = g32.get_state()
+    assert rel_l2(a32[0], ref_n) <= TOL32
