@@ -42,7 +42,7 @@ E2E_STEPS = 2000  # one full solve of the 1024^2 configuration per e2e iteration
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=32)
@@ -77,7 +77,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-i", str(self.index), "-lms", "200"],
+                 "-i", str(self.index), "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -120,6 +120,23 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------
 # helpers
+
+def reduce_max(x: float, device=None) -> float:
+    """Max of x over all ranks (identity on one process).  Works with the
+    gloo (CPU tensor) and nccl (CUDA tensor) backends."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Replicas: every rank does the same work; the job rate is all ranks'
+    units over the slowest rank's time."""
+    return world * units_per_rank / seconds_max
 
 def peaks():
     try:
@@ -253,19 +270,14 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-    ms = e0.elapsed_time(e1)
+    ms = reduce_max(e0.elapsed_time(e1), dev)
     prof = P.pss_profile_read(g.h)
     P.pss_set_profiling(g.h, False)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     mass1 = g.conserved()[:, 0]
     total_steps = args.warmup + args.steps
     drift = float(np.max(np.abs(mass1 - mass0) / mass0))
 
-    value = world * B * n * n * args.steps / (ms / 1e3) / 1e9
+    value = whole_job_rate(B * n * n * args.steps, world, ms / 1e3) / 1e9
 
     # roofline of the dominant kernel (row or column pass): algorithmic bytes =
     # one read + one write of the complex64 state per pass
@@ -328,15 +340,10 @@ def run_ours(args):
         for _ in range(iters):
             solve()
         torch.cuda.synchronize(dev)
-        te = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = reduce_max(time.perf_counter() - t0, dev)
         nbytes = B * n * n * 8
         drift2000 = float(np.max(np.abs(cq[0::2] - mass0) / mass0))
-        e2e = {"value": world * B * n * n * E2E_STEPS * iters / te / 1e9, "unit": UNIT,
+        e2e = {"value": whole_job_rate(B * n * n * E2E_STEPS * iters, world, te) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": nbytes / E2E_STEPS, "d2h_bytes_per_step": (nbytes + 16 * B) / E2E_STEPS,
                "per_solve": {"steps": E2E_STEPS, "h2d_bytes": nbytes, "d2h_bytes": nbytes + 16 * B,
                              "seconds": te / iters, "mass_drift_max_rel": drift2000}}

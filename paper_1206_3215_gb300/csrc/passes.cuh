@@ -26,11 +26,19 @@ namespace pss {
 // ----------------------------------------------------------------------------
 // Per (precision, length) launch shapes.  The PSS_* macros let a build pick
 // other shapes (points per thread, threads per CTA, resident CTAs per SM).
+// Measured at 1024^2 on GB300: 32 points per thread (two radix-32 stages, one
+// exchange) is 18% faster than 16 in FP32; FP64 prefers 16.
 #ifndef PSS_ROW_P
-#define PSS_ROW_P 16
+#define PSS_ROW_P 32
 #endif
 #ifndef PSS_COL_P
-#define PSS_COL_P 16
+#define PSS_COL_P 32
+#endif
+#ifndef PSS_ROW_P64
+#define PSS_ROW_P64 16
+#endif
+#ifndef PSS_COL_P64
+#define PSS_COL_P64 16
 #endif
 #ifndef PSS_ROW_THREADS
 #define PSS_ROW_THREADS 256
@@ -44,8 +52,10 @@ namespace pss {
 template <class Rl> struct Shape {
     static constexpr int ESZ = 2 * int(sizeof(Rl));
     // points per thread of the row and column transforms
-    __host__ __device__ static constexpr int rowP(int n) { return n < PSS_ROW_P ? n : PSS_ROW_P; }
-    __host__ __device__ static constexpr int colP(int n) { return n < PSS_COL_P ? n : PSS_COL_P; }
+    static constexpr int RP = sizeof(Rl) == 4 ? PSS_ROW_P : PSS_ROW_P64;
+    static constexpr int CP = sizeof(Rl) == 4 ? PSS_COL_P : PSS_COL_P64;
+    __host__ __device__ static constexpr int rowP(int n) { return n < RP ? n : RP; }
+    __host__ __device__ static constexpr int colP(int n) { return n < CP ? n : CP; }
     // rows per tile: about PSS_ROW_THREADS threads per CTA
     __host__ __device__ static constexpr int rows(int n)
     {
