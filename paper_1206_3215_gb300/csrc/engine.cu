@@ -1,5 +1,6 @@
 // Stepping drivers: which passes run, in which order, on which buffers.
 #include <cuda_runtime.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <cmath>
@@ -76,6 +77,10 @@ int pss_grid::init()
         if ((rc = cuda(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking), "stream"))) return rc;
         own_stream = true;
     }
+    {
+        const char *gr = getenv("PSS_GRAPHS");
+        use_graphs = !(gr && gr[0] == '0');
+    }
     // work arrays
     nbuf = p.eq == PSS_EQ_NLS ? 3 : p.eq == PSS_EQ_SG ? 5 : 7;
     for (int i = 0; i < nbuf; ++i)
@@ -150,6 +155,7 @@ int pss_grid::sync()
 {
     int rc = cuda(cudaStreamSynchronize(stream), "stream sync");
     if (rc) return rc;
+    if ((rc = check_ns_nonconv())) return rc;
     if (nonconv_pending) {
         nonconv_pending = false;
         return fail(PSS_E_NOT_CONVERGED, "NS fixed point reached max_iter=%d", p.max_iter);
@@ -208,6 +214,26 @@ int pss_grid::ns_update_count(int64_t *n)
     const NsFieldHost *f = static_cast<const NsFieldHost *>(host_fields);
     for (int64_t i = 0; i < batch; ++i) *n += f[i].updates;
     return PSS_OK;
+}
+
+// Report (and clear) fields that reached max_iter since the last check.
+int pss_grid::check_ns_nonconv()
+{
+    if (p.eq != PSS_EQ_NS || !has_state) return PSS_OK;
+    const size_t bytes = size_t(batch) * ns_field_bytes();
+    int rc = cuda(cudaMemcpyAsync(host_fields, ns_field, bytes, cudaMemcpyDeviceToHost, stream), "fields copy");
+    if (rc || (rc = cuda(cudaStreamSynchronize(stream), "sync"))) return rc;
+    NsFieldHost *h = static_cast<NsFieldHost *>(host_fields);
+    bool nc = false;
+    for (int64_t i = 0; i < batch; ++i) {
+        nc = nc || h[i].nonconv;
+        h[i].nonconv = 0;
+    }
+    if (!nc) return PSS_OK;
+    if ((rc = cuda(cudaMemcpyAsync(ns_field, h, bytes, cudaMemcpyHostToDevice, stream), "fields copy")) ||
+        (rc = cuda(cudaStreamSynchronize(stream), "sync")))
+        return rc;
+    return fail(PSS_E_NOT_CONVERGED, "NS fixed point reached max_iter=%d", p.max_iter);
 }
 
 // ----------------------------------------------------------------------------
@@ -476,61 +502,102 @@ template <class Rl> int ns_set(pss_grid *g, const void *w0, int where)
     return where == PSS_HOST ? g->cuda(cudaStreamSynchronize(g->stream), "sync") : PSS_OK;
 }
 
-template <class Rl> int ns_step(pss_grid *g, int64_t n)
+// the passes of one fixed-point update (row pass, column pass, decide, advance)
+template <class Rl> int ns_update(pss_grid *g, bool in_graph)
 {
     V2<Rl> *w[3];
     ns_w<Rl>(g, w);
-    int *flag = reinterpret_cast<int *>(g->flags);
-    int *hflag = reinterpret_cast<int *>(g->host_flags);
+    int *ctl = reinterpret_cast<int *>(g->flags);
     const double parseval = g->p.lx * g->p.ly / (double(g->npts) * double(g->npts));
     int rc;
+    if (!in_graph && (rc = g->pass_begin(0))) return rc;
+    cudaError_t e = ns_row_pass<Rl>(B<Rl>(g, 4), B<Rl>(g, 5), g->ns_field, g->nx, g->ny, g->batch,
+                                    Tw<Rl>(g->twx), g->stream);
+    if ((!in_graph && (rc = g->pass_end())) || (rc = g->cuda(e, "ns row pass"))) return rc;
+    int groups = 0;
+    if (!in_graph && (rc = g->pass_begin(1))) return rc;
+    e = ns_col_pass<Rl>(B<Rl>(g, 4), B<Rl>(g, 5), w, B<Rl>(g, 3), g->ns_field, g->partials, Rt<Rl>(g->kxo),
+                        Rt<Rl>(g->kyo), Rt<Rl>(g->kx2), Rt<Rl>(g->ky2), Rt<Rl>(g->keepx), Rt<Rl>(g->keepy), g->p.dt,
+                        g->p.nu, g->nx, g->ny, g->batch, ctl, Tw<Rl>(g->twy), &groups, g->stream);
+    if ((!in_graph && (rc = g->pass_end())) || (rc = g->cuda(e, "ns column pass"))) return rc;
+    if (!in_graph && (rc = g->pass_begin(2))) return rc;
+    e = ns_decide(g->ns_field, g->partials, groups, g->batch, ctl, parseval, g->p.tol, g->p.max_iter, g->stream);
+    if (e == cudaSuccess) e = ns_advance(ctl, in_graph, g->ns_cond, g->stream);
+    if ((!in_graph && (rc = g->pass_end())) || (rc = g->cuda(e, "ns decide"))) return rc;
+    return PSS_OK;
+}
+
+// One step as a graph: begin, then WHILE(some field active) { one update }.
+template <class Rl> int ns_build_graph(pss_grid *g)
+{
+    int *ctl = reinterpret_cast<int *>(g->flags);
+    cudaGraph_t graph = nullptr;
+    int rc;
+    if ((rc = g->cuda(cudaGraphCreate(&graph, 0), "graph create"))) return rc;
+    g->ns_graph = graph;
+    if ((rc = g->cuda(cudaGraphConditionalHandleCreate(&g->ns_cond, graph, 1, cudaGraphCondAssignDefault),
+                      "conditional handle")))
+        return rc;
+    if ((rc = g->cuda(cudaStreamBeginCaptureToGraph(g->stream, graph, nullptr, nullptr, 0,
+                                                    cudaStreamCaptureModeRelaxed), "capture")))
+        return rc;
+    cudaError_t e = ns_begin(g->ns_field, g->batch, ctl, g->stream);
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(g->stream, &out);
+    if ((rc = g->cuda(e != cudaSuccess ? e : e2, "capture begin"))) return rc;
+    cudaGraphNode_t begin_node = nullptr;
+    size_t count = 1;
+    if ((rc = g->cuda(cudaGraphGetNodes(graph, &begin_node, &count), "graph nodes"))) return rc;
+    // zero-initialised node parameters (the struct's union has no default constructor)
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
+    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = g->ns_cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode = nullptr;
+    if ((rc = g->cuda(cudaGraphAddNode(&cnode, graph, &begin_node, nullptr, 1, &cp), "conditional node"))) return rc;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((rc = g->cuda(cudaStreamBeginCaptureToGraph(g->stream, body, nullptr, nullptr, 0,
+                                                    cudaStreamCaptureModeRelaxed), "capture body")))
+        return rc;
+    rc = ns_update<Rl>(g, true);
+    e2 = cudaStreamEndCapture(g->stream, &out);
+    if (rc) return rc;
+    if ((rc = g->cuda(e2, "capture body end"))) return rc;
+    return g->cuda(cudaGraphInstantiate(&g->ns_exec, graph, 0), "graph instantiate");
+}
+
+template <class Rl> int ns_step(pss_grid *g, int64_t n)
+{
+    int *ctl = reinterpret_cast<int *>(g->flags);
+    int *hctl = reinterpret_cast<int *>(g->host_flags);
+    int rc;
+    if (g->use_graphs && !g->profiling && !g->ns_exec && ns_build_graph<Rl>(g) != PSS_OK) {
+        // capture is not available here: keep stepping with direct launches
+        g->use_graphs = false;
+        cudaGetLastError();
+        g->err.clear();
+    }
+    if (g->use_graphs && !g->profiling) {
+        for (int64_t s = 0; s < n; ++s)
+            if ((rc = g->cuda(cudaGraphLaunch(g->ns_exec, g->stream), "graph launch"))) return rc;
+        return PSS_OK;  // a field that reached max_iter is reported by the next synchronising call
+    }
     for (int64_t s = 0; s < n; ++s) {
-        if ((rc = g->cuda(ns_begin(g->ns_field, g->batch, flag, g->stream), "ns begin"))) return rc;
+        if ((rc = g->cuda(ns_begin(g->ns_field, g->batch, ctl, g->stream), "ns begin"))) return rc;
         for (int k = 0; k < g->p.max_iter; ++k) {
-            if ((rc = g->pass_begin(0))) return rc;
-            cudaError_t e = ns_row_pass<Rl>(B<Rl>(g, 4), B<Rl>(g, 5), g->ns_field, g->nx, g->ny, g->batch,
-                                            Tw<Rl>(g->twx), g->stream);
-            if ((rc = g->pass_end()) || (rc = g->cuda(e, "ns row pass"))) return rc;
-            int groups = 0;
-            if ((rc = g->pass_begin(1))) return rc;
-            e = ns_col_pass<Rl>(B<Rl>(g, 4), B<Rl>(g, 5), w, B<Rl>(g, 3), g->ns_field, g->partials, Rt<Rl>(g->kxo),
-                                Rt<Rl>(g->kyo), Rt<Rl>(g->kx2), Rt<Rl>(g->ky2), Rt<Rl>(g->keepx), Rt<Rl>(g->keepy),
-                                g->p.dt, g->p.nu, g->nx, g->ny, g->batch, k, Tw<Rl>(g->twy), &groups, g->stream);
-            if ((rc = g->pass_end()) || (rc = g->cuda(e, "ns column pass"))) return rc;
-            if ((rc = g->pass_begin(2))) return rc;
-            e = cudaMemsetAsync(flag, 0, sizeof(int), g->stream);
-            if (e == cudaSuccess)
-                e = ns_decide(g->ns_field, g->partials, groups, g->batch, k, parseval, g->p.tol, g->p.max_iter, flag,
-                              g->stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, g->stream);
-            if ((rc = g->pass_end()) || (rc = g->cuda(e, "ns decide"))) return rc;
-            if ((rc = g->cuda(cudaStreamSynchronize(g->stream), "ns sync"))) return rc;
-            if (*hflag == 0) break;
+            if ((rc = ns_update<Rl>(g, false))) return rc;
+            if ((rc = g->cuda(cudaMemcpyAsync(hctl, ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, g->stream),
+                              "ctl copy")) ||
+                (rc = g->cuda(cudaStreamSynchronize(g->stream), "ns sync")))
+                return rc;
+            if (hctl[2] == 0) break;
         }
     }
-    // report fields that hit max_iter
-    if ((rc = g->cuda(cudaMemcpyAsync(g->host_fields, g->ns_field, size_t(g->batch) * ns_field_bytes(),
-                                      cudaMemcpyDeviceToHost, g->stream), "fields copy")) ||
-        (rc = g->cuda(cudaStreamSynchronize(g->stream), "sync")))
-        return rc;
-    const NsFieldHost *f = static_cast<const NsFieldHost *>(g->host_fields);
-    bool nc = false;
-    for (int64_t i = 0; i < g->batch; ++i) nc = nc || f[i].nonconv;
-    if (nc) {
-        // clear the sticky flags so that only new failures are reported later
-        if ((rc = g->cuda(cudaMemcpyAsync(g->host_fields, g->ns_field, size_t(g->batch) * ns_field_bytes(),
-                                          cudaMemcpyDeviceToHost, g->stream), "fields copy")))
-            return rc;
-        NsFieldHost *h = static_cast<NsFieldHost *>(g->host_fields);
-        for (int64_t i = 0; i < g->batch; ++i) h[i].nonconv = 0;
-        if ((rc = g->cuda(cudaMemcpyAsync(g->ns_field, h, size_t(g->batch) * ns_field_bytes(), cudaMemcpyHostToDevice,
-                                          g->stream), "fields copy")) ||
-            (rc = g->cuda(cudaStreamSynchronize(g->stream), "sync")))
-            return rc;
-        g->steps += n;
-        return g->fail(PSS_E_NOT_CONVERGED, "NS fixed point reached max_iter=%d", g->p.max_iter);
-    }
-    return PSS_OK;
+    rc = g->check_ns_nonconv();
+    if (rc == PSS_E_NOT_CONVERGED) g->steps += n;  // the steps were taken; pss_grid::step_n adds n only on success
+    return rc;
 }
 
 // current vorticity of every field into buf[6]
@@ -601,7 +668,43 @@ int pss_grid::step_n(int64_t n)
 #define NLS(R) nls_step<R>(this, n)
 #define SG(R) sg_step<R>(this, n)
 #define NS(R) ns_step<R>(this, n)
-    rc = p.eq == PSS_EQ_NLS ? PSS_BY_PRECISION(NLS) : p.eq == PSS_EQ_SG ? PSS_BY_PRECISION(SG) : PSS_BY_PRECISION(NS);
+    if (p.eq != PSS_EQ_NS && use_graphs && !profiling) {
+        // the whole launch sequence of step_n(n) as one graph, cached by n
+        cudaGraphExec_t exec = nullptr;
+        for (auto &e : step_graphs)
+            if (e.first == n) exec = e.second;
+        if (!exec) {
+            rc = cuda(cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed), "capture");
+            if (!rc) {
+                const int64_t saved = launches;
+                int inner = p.eq == PSS_EQ_NLS ? PSS_BY_PRECISION(NLS) : PSS_BY_PRECISION(SG);
+                launches = saved;
+                cudaGraph_t graph = nullptr;
+                cudaError_t e = cudaStreamEndCapture(stream, &graph);
+                if (inner) rc = inner;
+                else if ((rc = cuda(e, "capture end")) == PSS_OK)
+                    rc = cuda(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+                if (graph) cudaGraphDestroy(graph);
+            }
+            if (rc) {
+                // capture is not available here: direct launches from now on
+                use_graphs = false;
+                cudaGetLastError();
+                err.clear();
+                rc = p.eq == PSS_EQ_NLS ? PSS_BY_PRECISION(NLS) : PSS_BY_PRECISION(SG);
+                if (!rc) steps += n;
+                return rc;
+            }
+            if (step_graphs.size() >= 4) {
+                cudaGraphExecDestroy(step_graphs.front().second);
+                step_graphs.erase(step_graphs.begin());
+            }
+            step_graphs.emplace_back(n, exec);
+        }
+        rc = cuda(cudaGraphLaunch(exec, stream), "graph launch");
+    } else {
+        rc = p.eq == PSS_EQ_NLS ? PSS_BY_PRECISION(NLS) : p.eq == PSS_EQ_SG ? PSS_BY_PRECISION(SG) : PSS_BY_PRECISION(NS);
+    }
 #undef NLS
 #undef SG
 #undef NS

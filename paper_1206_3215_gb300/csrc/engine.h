@@ -56,6 +56,13 @@ struct pss_grid {
     int pass_end();
     int profile_resolve();
 
+    // captured CUDA graphs (off while profiling, or with PSS_GRAPHS=0)
+    bool use_graphs = true;
+    cudaGraph_t ns_graph = nullptr;       // one NS step: begin -> WHILE(active) { passes }
+    cudaGraphExec_t ns_exec = nullptr;
+    cudaGraphConditionalHandle ns_cond = 0;
+    std::vector<std::pair<int64_t, cudaGraphExec_t>> step_graphs;  // NLS/SG step_n(n), by n
+
     int64_t steps = 0;
     bool has_state = false;
     bool nonconv_pending = false;
@@ -78,7 +85,14 @@ struct pss_grid {
     {
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         ev_pool.clear();
+        if (ns_exec) cudaGraphExecDestroy(ns_exec);
+        if (ns_graph) cudaGraphDestroy(ns_graph);
+        for (auto &g : step_graphs) cudaGraphExecDestroy(g.second);
+        step_graphs.clear();
+        ns_exec = nullptr;
+        ns_graph = nullptr;
     }
+    int check_ns_nonconv();
 
     size_t field_bytes() const { return size_t(ntot) * esz; }
     double dA() const { return (p.lx / double(nx)) * (p.ly / double(ny)); }

@@ -60,15 +60,18 @@ cudaError_t ns_row_pass(V2<Rl> *c1, V2<Rl> *c2, const void *fs, int64_t nx, int6
 template <class Rl>
 cudaError_t ns_col_pass(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, void *fs, double *partials,
                         const Rl *kxo, const Rl *kyo, const Rl *kx2, const Rl *ky2, const Rl *keepx,
-                        const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch, int k,
-                        const TW<Rl> *twy, int *groups_out, cudaStream_t s);
+                        const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch,
+                        const int *ctl, const TW<Rl> *twy, int *groups_out, cudaStream_t s);
 template <class Rl>
 cudaError_t ns_prep_pass(const V2<Rl> *w, V2<Rl> *c1, V2<Rl> *c2, const Rl *kxo, const Rl *kyo,
                          const Rl *kx2, const Rl *ky2, int64_t nx, int64_t ny, int64_t batch,
                          const TW<Rl> *twy, cudaStream_t s);
-cudaError_t ns_begin(void *fs, int64_t batch, int *any_active, cudaStream_t s);
-cudaError_t ns_decide(void *fs, const double *partials, int64_t groups, int64_t batch, int k, double parseval,
-                      double tol, int max_iter, int *any_active, cudaStream_t s);
+// loop control ctl (4 ints on the device): [0] update index, [1] any field
+// active after the current update, [2] its value at the last advance
+cudaError_t ns_begin(void *fs, int64_t batch, int *ctl, cudaStream_t s);
+cudaError_t ns_decide(void *fs, const double *partials, int64_t groups, int64_t batch, int *ctl, double parseval,
+                      double tol, int max_iter, cudaStream_t s);
+cudaError_t ns_advance(int *ctl, bool use_graph, cudaGraphConditionalHandle h, cudaStream_t s);
 
 // ---- elementwise helpers (k_util.cu) ----------------------------------------
 template <class Rl> cudaError_t real_to_complex(const Rl *src, V2<Rl> *dst, int64_t n, bool apply_sin, cudaStream_t s);

@@ -80,7 +80,8 @@ template <class Rl> struct NsCol {
     const Rl *kxo, *kyo, *kx2, *ky2, *keepx, *keepy;
     Rl half_dt, half_dt_nu, inv_n2;
     int64_t nx;
-    int k, W;
+    const int *kptr;  // fixed-point update index of this pass (device, set by k_ns_advance)
+    int W;
     __device__ const V2<Rl> *in(int) const { return c1; }
     __device__ V2<Rl> *wb(int b) const { return b == 0 ? w0 : b == 1 ? w1 : w2; }
     template <int N, int P, bool BLOCK, class Sm>
@@ -89,6 +90,7 @@ template <class Rl> struct NsCol {
     {
         constexpr int T = N / P;
         V2<Rl>(&v)[P] = vv[0];
+        const int k = *kptr;
         const NsField f = fs[field];
         const bool live = f.active != 0;
         const int64_t base = field * N * nx + x;
@@ -185,12 +187,17 @@ template <class Rl> struct NsPrep {
     }
 };
 
+// Device-side loop control, 4 ints: [0] update index k of the current pass,
+// [1] any field still active after this update (built by k_ns_decide),
+// [2] the value of [1] at the last k_ns_advance (read by the host loop).
 // one thread per field: fold the partials of update k, decide, count
-__global__ void k_ns_decide(NsField *fs, const double *partials, int64_t groups, int64_t batch, int k,
-                            double parseval, double tol, int max_iter, int *any_active)
+__global__ void k_ns_decide(NsField *fs, const double *partials, int64_t groups, int64_t batch, int *ctl,
+                            double parseval, double tol, int max_iter)
 {
     const int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (f >= batch) return;
+    const int k = ctl[0];
+    int *any_active = ctl + 1;
     NsField s = fs[f];
     if (!s.active) return;
     double sum = 0.0;
@@ -208,11 +215,26 @@ __global__ void k_ns_decide(NsField *fs, const double *partials, int64_t groups,
     fs[f] = s;
 }
 
-__global__ void k_ns_begin(NsField *fs, int64_t batch, int *any_active)
+__global__ void k_ns_begin(NsField *fs, int64_t batch, int *ctl)
 {
     const int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (f == 0) *any_active = 0;
+    if (f == 0) {
+        ctl[0] = 0;
+        ctl[1] = 0;
+    }
     if (f < batch) fs[f].active = 1;
+}
+
+// next update: k += 1; the loop continues while some field is active.  Inside
+// a captured step graph this sets the WHILE node's condition; every field
+// stops at max_iter at the latest, so the loop always ends.
+__global__ void k_ns_advance(int *ctl, int use_graph, cudaGraphConditionalHandle h)
+{
+    const int more = ctl[1] != 0;
+    ctl[2] = more;
+    ctl[1] = 0;
+    ctl[0] += 1;
+    if (use_graph) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 template <class Rl>
@@ -225,11 +247,11 @@ cudaError_t ns_row_pass(V2<Rl> *c1, V2<Rl> *c2, const void *fs, int64_t nx, int6
 template <class Rl>
 cudaError_t ns_col_pass(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, void *fs, double *partials,
                         const Rl *kxo, const Rl *kyo, const Rl *kx2, const Rl *ky2, const Rl *keepx,
-                        const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch, int k,
-                        const TW<Rl> *twy, int *groups_out, cudaStream_t s)
+                        const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch,
+                        const int *ctl, const TW<Rl> *twy, int *groups_out, cudaStream_t s)
 {
     NsCol<Rl> op{c1, c2, w[0], w[1], w[2], jn, static_cast<NsField *>(fs), partials, kxo, kyo, kx2, ky2,
-                 keepx, keepy, Rl(0.5 * dt), Rl(0.5 * dt * nu), Rl(1.0 / (double(nx) * double(ny))), nx, k, 0};
+                 keepx, keepy, Rl(0.5 * dt), Rl(0.5 * dt * nu), Rl(1.0 / (double(nx) * double(ny))), nx, ctl, 0};
     switch (ny) {
 #define PSS_CASE(N)                                         \
     case N:                                                 \
@@ -251,17 +273,23 @@ cudaError_t ns_prep_pass(const V2<Rl> *w, V2<Rl> *c1, V2<Rl> *c2, const Rl *kxo,
     return launch_col<Rl>(ny, nx, op, twy, batch, s);
 }
 
-cudaError_t ns_begin(void *fs, int64_t batch, int *any_active, cudaStream_t s)
+cudaError_t ns_begin(void *fs, int64_t batch, int *ctl, cudaStream_t s)
 {
-    k_ns_begin<<<unsigned((batch + 255) / 256), 256, 0, s>>>(static_cast<NsField *>(fs), batch, any_active);
+    k_ns_begin<<<unsigned((batch + 255) / 256), 256, 0, s>>>(static_cast<NsField *>(fs), batch, ctl);
     return cudaGetLastError();
 }
 
-cudaError_t ns_decide(void *fs, const double *partials, int64_t groups, int64_t batch, int k, double parseval,
-                      double tol, int max_iter, int *any_active, cudaStream_t s)
+cudaError_t ns_decide(void *fs, const double *partials, int64_t groups, int64_t batch, int *ctl, double parseval,
+                      double tol, int max_iter, cudaStream_t s)
 {
     k_ns_decide<<<unsigned((batch + 255) / 256), 256, 0, s>>>(static_cast<NsField *>(fs), partials, groups,
-                                                             batch, k, parseval, tol, max_iter, any_active);
+                                                             batch, ctl, parseval, tol, max_iter);
+    return cudaGetLastError();
+}
+
+cudaError_t ns_advance(int *ctl, bool use_graph, cudaGraphConditionalHandle h, cudaStream_t s)
+{
+    k_ns_advance<<<1, 1, 0, s>>>(ctl, use_graph ? 1 : 0, h);
     return cudaGetLastError();
 }
 
@@ -272,8 +300,8 @@ size_t ns_field_bytes() { return sizeof(NsField); }
                                          const TW<Rl> *, cudaStream_t);                                      \
     template cudaError_t ns_col_pass<Rl>(V2<Rl> *, V2<Rl> *, V2<Rl> *const[3], V2<Rl> *, void *, double *,  \
                                          const Rl *, const Rl *, const Rl *, const Rl *, const Rl *,         \
-                                         const Rl *, double, double, int64_t, int64_t, int64_t, int,        \
-                                         const TW<Rl> *, int *, cudaStream_t);                              \
+                                         const Rl *, double, double, int64_t, int64_t, int64_t,             \
+                                         const int *, const TW<Rl> *, int *, cudaStream_t);                 \
     template cudaError_t ns_prep_pass<Rl>(const V2<Rl> *, V2<Rl> *, V2<Rl> *, const Rl *, const Rl *,        \
                                           const Rl *, const Rl *, int64_t, int64_t, int64_t, const TW<Rl> *, \
                                           cudaStream_t);

@@ -122,8 +122,11 @@ def test_non_convergence_is_reported_and_handle_stays_usable(lib, cuda_device):
     n, L = 32, 2 * math.pi
     g = lib.Grid("ns", n, "fp64", lx=L, ly=L, dt=2.5e-3, nu=1e-3, max_iter=1)
     g.set_state(S.ns_power_law(n)[None])
+    # reported by step_n itself (direct launches) or by the next synchronising
+    # call (a captured step graph loops on the device)
     with pytest.raises(lib.PssError) as e:
         g.step(3)
+        g.sync()
     assert e.value.code == lib.PSS_E_NOT_CONVERGED
     assert np.isfinite(g.get_state()).all()
     assert g.stats()[1] == 3
@@ -140,3 +143,29 @@ def test_circulation_is_conserved_at_config4_size(lib, cuda_device):
     (c1, z1, e1), = g.conserved()
     assert abs(c1 - c0) <= 1e-9 * math.sqrt(z0) * L
     assert z1 <= z0 * (1 + 1e-6) and e1 <= e0 * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("eq", ["ns", "nls", "sg"])
+def test_graph_and_direct_launches_agree_bitwise(lib, cuda_device, eq, monkeypatch):
+    # the step as one captured CUDA graph (NS: a device-side WHILE loop over
+    # the fixed-point updates) equals the step launched kernel by kernel
+    n = 64
+    if eq == "ns":
+        kw, state = dict(lx=2 * math.pi, ly=2 * math.pi, dt=2.5e-3, nu=1e-3), (S.ns_power_law(n, batch=2),)
+    elif eq == "nls":
+        kw, state = dict(dt=1e-3), (S.nls_gaussian(n, batch=2),)
+    else:
+        kw, state = dict(lx=10 * math.pi, ly=10 * math.pi, dt=1e-3), S.sg_gaussian(n, batch=2)
+    out = []
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("PSS_GRAPHS", graphs)
+        g = lib.Grid(eq, n, "fp32", batch=2, **kw)
+        g.set_state(*state)
+        g.step(7)
+        g.step(7)
+        r = g.get_state()
+        out.append((r if isinstance(r, tuple) else (r,), g.stats()))
+        g.close()
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, b)
+    assert out[0][1] == out[1][1]
