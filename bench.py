@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=120)
     return ap.parse_args()
 
 
@@ -349,6 +351,20 @@ def run_ours(args):
                              "seconds": te / iters, "mass_drift_max_rel": drift2000}}
         ge.close()
 
+    # served latency: a seeded Poisson stream of mixed NLS / SG / NS solves
+    # (N in 128..2048, 50-500 steps, FP32) through the continuous-batching server
+    serve = None
+    if not args.no_serve:
+        from paper_1206_3215_gb300.serving import Request, Server
+        mix = [Request.from_dict(d) for d in S.serving_mix(args.serve_requests, 40.0, seed=S.SEED_BASE + 4 + rank)]
+        srv = Server(slots=8, round_max=50)
+        _, st = srv.run(mix, realtime=True, timeout=300)
+        srv.close()
+        serve = {"requests": st["requests"], "arrival_rate_hz": 40.0, "p50_latency_ms": st["p50_latency_s"] * 1e3,
+                 "p99_latency_ms": st["p99_latency_s"] * 1e3, "throughput_gpt_steps_s": st["gpt_steps_per_s"],
+                 "wall_s": st["wall_s"], "pools": st["pools"], "rounds": st["rounds"],
+                 "mix": "NLS/SG/NS FP32, N in {128,256,512,1024,2048}, 50-500 steps, 8 slots per pool"}
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         try:
@@ -371,6 +387,7 @@ def run_ours(args):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "serving": serve,
             "gpu_launches": prof["launches"],
             "clocks": clk.summary(),
         }

@@ -122,6 +122,17 @@ int pss_step_n(pss_grid *g, int64_t n);
  *  NS:  a = omega^n (real).  Synchronises. */
 int pss_get_state(pss_grid *g, void *a, void *b, int where);
 
+/* One field of the batch (a slot), for callers that manage fields
+ * independently (continuous batching): the same layouts as pss_set_state /
+ * pss_get_state for a single [ny][nx] field, with the same set-up of the
+ * equation's state for that field only; the other fields are untouched.
+ * pss_set_field does not change the grid's step counter.  Work is enqueued on
+ * the grid's stream; pss_set_field synchronises for HOST input,
+ * pss_get_field always.  Fields never set hold zeros (a fixed point of all
+ * three equations).  Errors: PSS_E_ARG (field out of range, null pointer). */
+int pss_set_field(pss_grid *g, int64_t field, const void *a, const void *b, int where);
+int pss_get_field(pss_grid *g, int64_t field, void *a, void *b, int where);
+
 /* Diagnostics of every field, in double, written to out[field * per + i]:
  *  NLS (per = 2): mass  = integral |psi|^2,
  *                 energy = integral |grad psi|^2 / 2 + sigma |psi|^4 / 4   (Eq. 2);

@@ -27,6 +27,7 @@ EXPORTED = [
     "pss_conserved_quantities", "pss_stats", "pss_checkpoint_size", "pss_checkpoint_save",
     "pss_checkpoint_load", "pss_sync", "pss_destroy", "pss_last_error", "pss_fft2d",
     "pss_version", "pss_set_profiling", "pss_profile_read", "pss_nls_invariants_static",
+    "pss_set_field", "pss_get_field",
 ]
 
 
@@ -83,6 +84,8 @@ def load_library(path: str = LIB_PATH):
             "pss_set_profiling": (I, [P, I]),
             "pss_profile_read": (I, [P, P, I, P]),
             "pss_nls_invariants_static": (I, [P, P, I64, I64, I64, D, D, D, I, P, P]),
+            "pss_set_field": (I, [P, I64, P, P, I]),
+            "pss_get_field": (I, [P, I64, P, P, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -124,6 +127,14 @@ def pss_step_n(h, n: int) -> None:
 
 def pss_get_state(h, a_ptr: int, b_ptr: int | None, where: int) -> None:
     _check(load_library().pss_get_state(h, a_ptr, b_ptr, where), h)
+
+
+def pss_set_field(h, field: int, a_ptr: int, b_ptr: int | None, where: int) -> None:
+    _check(load_library().pss_set_field(h, field, a_ptr, b_ptr, where), h)
+
+
+def pss_get_field(h, field: int, a_ptr: int, b_ptr: int | None, where: int) -> None:
+    _check(load_library().pss_get_field(h, field, a_ptr, b_ptr, where), h)
 
 
 def pss_conserved_quantities(h, cap: int = 3 * 65535) -> np.ndarray:
@@ -272,6 +283,31 @@ class Grid:
             pss_get_state(self.h, a.ctypes.data, b.ctypes.data, PSS_HOST)
             return a, b
         pss_get_state(self.h, a.ctypes.data, None, PSS_HOST)
+        return a
+
+    def set_field(self, field: int, a, b=None):
+        """Set one field (slot) of the batch from host arrays of shape [ny][nx]."""
+        complex_ = self.eq == "nls"
+        dt = self.complex_dtype if complex_ else self.real_dtype
+        a = np.ascontiguousarray(np.asarray(a, dtype=dt))
+        bb = None if b is None else np.ascontiguousarray(np.asarray(b, dtype=dt))
+        if a.size != self.nx * self.ny or (bb is not None and bb.size != a.size):
+            raise ValueError("bad field size")
+        pss_set_field(self.h, field, a.ctypes.data, None if bb is None else bb.ctypes.data, PSS_HOST)
+
+    def get_field(self, field: int):
+        """Host copy of one field: NLS psi; SG (u^n, u^{n-1}); NS omega."""
+        shape = (self.ny, self.nx)
+        if self.eq == "nls":
+            a = np.empty(shape, self.complex_dtype)
+            pss_get_field(self.h, field, a.ctypes.data, None, PSS_HOST)
+            return a
+        a = np.empty(shape, self.real_dtype)
+        if self.eq == "sg":
+            b = np.empty(shape, self.real_dtype)
+            pss_get_field(self.h, field, a.ctypes.data, b.ctypes.data, PSS_HOST)
+            return a, b
+        pss_get_field(self.h, field, a.ctypes.data, None, PSS_HOST)
         return a
 
     def get_state_device(self, out_a, out_b=None):

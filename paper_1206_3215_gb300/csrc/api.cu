@@ -200,6 +200,25 @@ int pss_get_state(pss_grid *g, void *a, void *b, int where)
     return g->get_state(a, b, where);
 }
 
+int pss_set_field(pss_grid *g, int64_t field, const void *a, const void *b, int where)
+{
+    if (!g) return PSS_E_ARG;
+    if (!a || field < 0 || field >= g->batch || (where != PSS_HOST && where != PSS_DEVICE))
+        return g->fail(PSS_E_ARG, "set_field: bad field, pointer or location");
+    DeviceGuard dg(g->dev);
+    return g->set_field(field, a, b, where);
+}
+
+int pss_get_field(pss_grid *g, int64_t field, void *a, void *b, int where)
+{
+    if (!g) return PSS_E_ARG;
+    if (!a || field < 0 || field >= g->batch || (where != PSS_HOST && where != PSS_DEVICE))
+        return g->fail(PSS_E_ARG, "get_field: bad field, pointer or location");
+    if (!g->has_state) return g->fail(PSS_E_STATE, "get_field before any state was set");
+    DeviceGuard dg(g->dev);
+    return g->get_field(field, a, b, where);
+}
+
 int pss_conserved_quantities(pss_grid *g, double *out, int cap, int *count)
 {
     if (!g) return PSS_E_ARG;

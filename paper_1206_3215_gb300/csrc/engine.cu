@@ -83,8 +83,10 @@ int pss_grid::init()
     }
     // work arrays
     nbuf = p.eq == PSS_EQ_NLS ? 3 : p.eq == PSS_EQ_SG ? 5 : 7;
-    for (int i = 0; i < nbuf; ++i)
+    for (int i = 0; i < nbuf; ++i) {
         if ((rc = alloc(&buf[i], field_bytes()))) return rc;
+        if ((rc = cuda(cudaMemset(buf[i], 0, field_bytes()), "memset"))) return rc;
+    }
     // tables
     if ((rc = upload_twiddles(this, nx, &twx))) return rc;
     if ((rc = upload_twiddles(this, ny, &twy))) return rc;
@@ -641,6 +643,116 @@ template <class Rl> int ns_conserved(pss_grid *g, double *out)
 }  // namespace
 
 // ----------------------------------------------------------------------------
+// One field of the batch (slot f): the set-up and read-back of the equation on
+// the sub-arrays of field f, with batch 1.
+
+namespace {
+
+template <class Rl> V2<Rl> *Bf(pss_grid *g, int i, int64_t f) { return B<Rl>(g, i) + f * g->npts; }
+
+template <class Rl> cudaError_t fft2_one(pss_grid *g, V2<Rl> *b, int dir)
+{
+    cudaError_t e = fft_rows<Rl>(b, g->nx, g->ny, dir, Rl(1), Tw<Rl>(g->twx), g->stream);
+    if (e != cudaSuccess) return e;
+    const Rl sc = dir > 0 ? Rl(1.0 / (double(g->nx) * double(g->ny))) : Rl(1);
+    return fft_cols<Rl>(b, g->nx, g->ny, 1, dir, sc, Tw<Rl>(g->twy), g->stream);
+}
+
+// real field (host or device) -> complex slot dst_buf[f], through raw scratch slot tmp_buf[f]
+template <class Rl>
+int load_real_one(pss_grid *g, int64_t f, const void *src, int where, int tmp, int dst, bool apply_sin)
+{
+    Rl *t = reinterpret_cast<Rl *>(Bf<Rl>(g, tmp, f));
+    int rc = g->cuda(cudaMemcpyAsync(t, src, size_t(g->npts) * sizeof(Rl), kind_in(where), g->stream), "copy");
+    if (rc) return rc;
+    return g->cuda(real_to_complex<Rl>(t, Bf<Rl>(g, dst, f), g->npts, apply_sin, g->stream), "real to complex");
+}
+
+template <class Rl> int store_real_one(pss_grid *g, int64_t f, const V2<Rl> *a, void *dst, int where, int tmp)
+{
+    Rl *d = where == PSS_DEVICE ? static_cast<Rl *>(dst) : reinterpret_cast<Rl *>(Bf<Rl>(g, tmp, f));
+    int rc = g->cuda(complex_to_real<Rl>(a, nullptr, Rl(0), d, g->npts, g->stream), "complex to real");
+    if (rc || where == PSS_DEVICE) return rc;
+    return g->cuda(cudaMemcpyAsync(dst, d, size_t(g->npts) * sizeof(Rl), cudaMemcpyDeviceToHost, g->stream), "copy");
+}
+
+template <class Rl> int field_set(pss_grid *g, int64_t f, const void *a, const void *b, int where)
+{
+    int rc = PSS_OK;
+    const size_t fb = size_t(g->npts) * g->esz;
+    if (g->p.eq == PSS_EQ_NLS) {
+        if ((rc = g->cuda(cudaMemcpyAsync(Bf<Rl>(g, 0, f), a, fb, kind_in(where), g->stream), "copy")) ||
+            (rc = g->cuda(fft_rows<Rl>(Bf<Rl>(g, 0, f), g->nx, g->ny, -1, Rl(1), Tw<Rl>(g->twx), g->stream), "row fft")))
+            return rc;
+    } else if (g->p.eq == PSS_EQ_SG) {
+        if ((rc = load_real_one<Rl>(g, f, a, where, 3, 0, false)) ||
+            (rc = g->cuda(real_to_complex<Rl>(reinterpret_cast<Rl *>(Bf<Rl>(g, 3, f)), Bf<Rl>(g, 2, f), g->npts, true,
+                                              g->stream), "sin")))
+            return rc;
+        if (b) rc = load_real_one<Rl>(g, f, b, where, 3, 1, false);
+        else rc = g->cuda(cudaMemsetAsync(Bf<Rl>(g, 1, f), 0, fb, g->stream), "memset");
+        if (rc) return rc;
+        for (int i : {0, 1, 2})
+            if ((rc = g->cuda(fft2_one<Rl>(g, Bf<Rl>(g, i, f), -1), "forward"))) return rc;
+        const Rl s = Rl(1.0 / (double(g->nx) * double(g->ny)));
+        if ((rc = g->cuda(sg_init<Rl>(Bf<Rl>(g, 0, f), Bf<Rl>(g, 1, f), Bf<Rl>(g, 2, f), g->kx2d, g->ky2d, g->p.dt,
+                                      g->nx, g->ny, 1, g->stream), "sg init")) ||
+            (rc = g->cuda(cudaMemcpyAsync(Bf<Rl>(g, 2, f), Bf<Rl>(g, 0, f), fb, cudaMemcpyDeviceToDevice, g->stream),
+                          "copy")) ||
+            (rc = g->cuda(fft_cols<Rl>(Bf<Rl>(g, 2, f), g->nx, g->ny, 1, +1, s, Tw<Rl>(g->twy), g->stream), "H")))
+            return rc;
+    } else {
+        if ((rc = load_real_one<Rl>(g, f, a, where, 6, 0, false)) ||
+            (rc = g->cuda(fft2_one<Rl>(g, Bf<Rl>(g, 0, f), -1), "forward")) ||
+            (rc = g->cuda(apply_mask<Rl>(Bf<Rl>(g, 0, f), Rt<Rl>(g->keepx), Rt<Rl>(g->keepy), g->nx, g->ny, 1,
+                                         g->stream), "mask")) ||
+            (rc = g->cuda(cudaMemsetAsync(static_cast<char *>(g->ns_field) + f * ns_field_bytes(), 0, ns_field_bytes(),
+                                          g->stream), "record")) ||
+            (rc = g->cuda(ns_prep_pass<Rl>(Bf<Rl>(g, 0, f), Bf<Rl>(g, 4, f), Bf<Rl>(g, 5, f), Rt<Rl>(g->kxo),
+                                           Rt<Rl>(g->kyo), Rt<Rl>(g->kx2), Rt<Rl>(g->ky2), g->nx, g->ny, 1,
+                                           Tw<Rl>(g->twy), g->stream), "ns derivatives")))
+            return rc;
+    }
+    return where == PSS_HOST ? g->cuda(cudaStreamSynchronize(g->stream), "sync") : PSS_OK;
+}
+
+template <class Rl> int field_get(pss_grid *g, int64_t f, void *a, void *b, int where)
+{
+    int rc;
+    const size_t fb = size_t(g->npts) * g->esz;
+    if (g->p.eq == PSS_EQ_NLS) {
+        if ((rc = g->cuda(cudaMemcpyAsync(Bf<Rl>(g, 1, f), Bf<Rl>(g, 0, f), fb, cudaMemcpyDeviceToDevice, g->stream),
+                          "copy")) ||
+            (rc = g->cuda(fft_rows<Rl>(Bf<Rl>(g, 1, f), g->nx, g->ny, +1, Rl(1.0 / double(g->nx)), Tw<Rl>(g->twx),
+                                       g->stream), "row inverse")) ||
+            (rc = g->cuda(cudaMemcpyAsync(a, Bf<Rl>(g, 1, f), fb, kind_out(where), g->stream), "copy")))
+            return rc;
+    } else if (g->p.eq == PSS_EQ_SG) {
+        if ((rc = g->cuda(cudaMemcpyAsync(Bf<Rl>(g, 3, f), Bf<Rl>(g, 0, f), fb, cudaMemcpyDeviceToDevice, g->stream),
+                          "copy")) ||
+            (rc = g->cuda(fft2_one<Rl>(g, Bf<Rl>(g, 3, f), +1), "inverse")) ||
+            (rc = store_real_one<Rl>(g, f, Bf<Rl>(g, 3, f), a, where, 4)))
+            return rc;
+        if (b && ((rc = g->cuda(cplx_axpy<Rl>(Bf<Rl>(g, 0, f), Bf<Rl>(g, 1, f), Rl(1), Bf<Rl>(g, 3, f), g->npts,
+                                              g->stream), "axpy")) ||
+                  (rc = g->cuda(fft2_one<Rl>(g, Bf<Rl>(g, 3, f), +1), "inverse")) ||
+                  (rc = store_real_one<Rl>(g, f, Bf<Rl>(g, 3, f), b, where, 4))))
+            return rc;
+    } else {
+        V2<Rl> *w[3];
+        for (int i = 0; i < 3; ++i) w[i] = Bf<Rl>(g, i, f);  // field f's slot of each vorticity buffer
+        if ((rc = g->cuda(ns_gather<Rl>(static_cast<char *>(g->ns_field) + f * ns_field_bytes(), w, Bf<Rl>(g, 6, f),
+                                        g->npts, 1, g->stream), "gather")) ||
+            (rc = g->cuda(fft2_one<Rl>(g, Bf<Rl>(g, 6, f), +1), "inverse")) ||
+            (rc = store_real_one<Rl>(g, f, Bf<Rl>(g, 6, f), a, where, 3)))
+            return rc;
+    }
+    return g->sync();
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
 // dispatch by equation and precision
 
 #define PSS_BY_PRECISION(CALL) (p.precision == PSS_FP32 ? CALL(float) : CALL(double))
@@ -721,6 +833,18 @@ int pss_grid::get_state(void *a, void *b, int where)
 #undef NLS
 #undef SG
 #undef NS
+}
+
+int pss_grid::set_field(int64_t f, const void *a, const void *b, int where)
+{
+    int rc = p.precision == PSS_FP32 ? field_set<float>(this, f, a, b, where) : field_set<double>(this, f, a, b, where);
+    if (!rc) has_state = true;
+    return rc;
+}
+
+int pss_grid::get_field(int64_t f, void *a, void *b, int where)
+{
+    return p.precision == PSS_FP32 ? field_get<float>(this, f, a, b, where) : field_get<double>(this, f, a, b, where);
 }
 
 int pss_grid::conserved(double *out)

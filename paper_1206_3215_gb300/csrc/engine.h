@@ -76,6 +76,8 @@ struct pss_grid {
     int set_state(const void *a, const void *b, int where);
     int step_n(int64_t n);
     int get_state(void *a, void *b, int where);
+    int set_field(int64_t f, const void *a, const void *b, int where);
+    int get_field(int64_t f, void *a, void *b, int where);
     int conserved(double *out);
     int sync();
     int ns_update_count(int64_t *n);

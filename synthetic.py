@@ -101,3 +101,32 @@ def taylor_green_2pi(n: int, t: float = 0.0, nu: float = 1e-3) -> np.ndarray:
     x = grid_coords(n, 0.0, 2 * math.pi)
     X, Y = np.meshgrid(x, x, indexing="xy")
     return 2 * np.sin(X) * np.sin(Y) * math.exp(-2 * nu * t)
+
+
+def serving_mix(count: int, rate_hz: float, sizes=(128, 256, 512, 1024, 2048), steps=(50, 500),
+                seed: int = SEED_BASE + 4, eqs=("nls", "sg", "ns")) -> list[dict]:
+    """Seeded Poisson stream of mixed solves (FP32): arrival times with mean
+    spacing 1/rate_hz, equation, grid size and step count uniform over the
+    given choices, each with its own seeded initial field and the parameters
+    of that equation's workload above."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for rid in range(count):
+        t += rng.exponential(1.0 / rate_hz)
+        eq = eqs[int(rng.integers(len(eqs)))]
+        n = int(sizes[int(rng.integers(len(sizes)))])
+        k = int(rng.integers(steps[0], steps[1] + 1))
+        fseed = int(rng.integers(1 << 30))
+        if eq == "nls":
+            state = (nls_gaussian(n, seed=fseed),)
+            params = {"dt": 1e-3, "lx": 20 * math.pi, "ly": 20 * math.pi}
+        elif eq == "sg":
+            state = sg_gaussian(n, seed=fseed)
+            params = {"dt": 1e-3, "lx": 10 * math.pi, "ly": 10 * math.pi}
+        else:
+            state = (ns_power_law(n, seed=fseed),)
+            params = {"dt": 2.5e-4, "lx": 2 * math.pi, "ly": 2 * math.pi, "nu": 1e-3}
+        out.append({"rid": rid, "eq": eq, "n": n, "steps": k, "state": state, "arrival": t,
+                    "precision": "fp32", "params": params})
+    return out

@@ -1,0 +1,73 @@
+"""Continuous batching: a mixed stream of NLS, sine-Gordon and Navier-Stokes
+solves served through shared batched grids gives every request the result it
+gets alone (SG and NS bit for bit; NLS within the FP32 tolerance, since the
+split-step merges half steps inside each pss_step_n call and the server cuts
+a solve into rounds)."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from gpu_util import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(results, reqs):
+    from paper_1206_3215_gb300.serving import solve_alone
+    for q in reqs:
+        got = results[q.rid].state
+        ref = solve_alone(q)
+        got = got if isinstance(got, tuple) else (got,)
+        ref = ref if isinstance(ref, tuple) else (ref,)
+        for a, b in zip(got, ref):
+            if q.eq == "nls":
+                assert rel_l2(a, b) <= 1e-5, (q.rid, rel_l2(a, b))
+            else:
+                assert np.array_equal(a, b), q.rid
+
+
+def test_mixed_stream_matches_solo_runs(lib, cuda_device):
+    from paper_1206_3215_gb300.serving import Request, Server
+    reqs = [Request.from_dict(d) for d in S.serving_mix(24, 1e6, sizes=(64, 128), steps=(20, 60))]
+    srv = Server(slots=4, round_max=16)
+    results, stats = srv.run(reqs, realtime=False)
+    srv.close()
+    assert len(results) == len(reqs)
+    assert stats["rounds"] > 0 and stats["p99_latency_s"] >= stats["p50_latency_s"] > 0
+    _check(results, reqs)
+
+
+def test_one_pool_at_a_time_still_serves_everything(lib, cuda_device):
+    # with room for a single pool, requests of other shapes wait and idle
+    # pools are released to admit them
+    from paper_1206_3215_gb300.serving import Request, Server
+    reqs = [Request.from_dict(d) for d in S.serving_mix(10, 1e6, sizes=(64, 128), steps=(10, 30), seed=99)]
+    srv = Server(slots=2, round_max=8, max_pools=1)
+    results, stats = srv.run(reqs, realtime=False)
+    srv.close()
+    assert len(results) == len(reqs)
+    _check(results, reqs)
+
+
+def test_realtime_arrivals_report_latency(lib, cuda_device):
+    from paper_1206_3215_gb300.serving import Request, Server
+    reqs = [Request.from_dict(d) for d in S.serving_mix(12, 200.0, sizes=(64,), steps=(10, 20), seed=7)]
+    srv = Server(slots=4, round_max=10)
+    results, stats = srv.run(reqs, realtime=True, timeout=120)
+    srv.close()
+    assert len(results) == 12
+    assert all(r.latency > 0 and r.queued >= 0 for r in results.values())
+
+
+def test_set_and_get_field_round_trip(lib, cuda_device):
+    n = 64
+    for eq, state in (("nls", (S.nls_gaussian(n),)), ("sg", S.sg_gaussian(n)), ("ns", (S.taylor_green_2pi(n),))):
+        g = lib.Grid(eq, n, "fp64", batch=3, lx=2 * np.pi, ly=2 * np.pi)
+        g.set_field(1, *state)
+        out = g.get_field(1)
+        a = out[0] if isinstance(out, tuple) else out
+        assert rel_l2(a, state[0]) <= 1e-13
+        # the other slots hold zeros
+        z = g.get_field(0)
+        z = z[0] if isinstance(z, tuple) else z
+        assert np.abs(z).max() == 0.0
