@@ -149,13 +149,16 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+# files that define the NLS pass kernels (and their launch shapes)
+NLS_KERNEL_FILES = ("fft_core.cuh", "passes.cuh", "launch.cuh", "internal.h", "k_nls.cu")
+
+
+def kernel_source_hash(files=NLS_KERNEL_FILES) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1206_3215_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode() + fh.read())
+    for f in files:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
