@@ -197,6 +197,15 @@ template <int P> __device__ __forceinline__ void fence(double2 (&v)[P])
     for (int m = 0; m < P; ++m) asm volatile("" : "+d"(v[m].x), "+d"(v[m].y));
 }
 
+// One copy of the forward transform can serve both transforms of a fused
+// pass: F^-1 x = conj(F conj x) exactly (negation is exact), which halves the
+// unrolled code and the registers it holds.
+template <int P, class V> __device__ __forceinline__ void conj_all(V (&v)[P])
+{
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m].y = -v[m].y;
+}
+
 template <bool BLOCK> __device__ __forceinline__ void fft_sync()
 {
     if constexpr (BLOCK) __syncthreads();

@@ -33,8 +33,16 @@ template <class Rl> __device__ __forceinline__ void phase_terms(Rl th, Rl &sn, R
     }
 }
 
+// FP32 runs both transforms through one forward-FFT body (fewer registers and
+// instruction-cache misses); FP64 keeps the two specialised bodies.
+#ifndef PSS_SHARED_FFT
+#define PSS_SHARED_FFT 1
+#endif
+
 template <class Rl> struct NlsRow {
     static constexpr int NIN = 1;
+    static constexpr bool LEAN = true;
+    static constexpr int PMAX = 32;
     V2<Rl> *data;
     Rl sigma_dt;
     __device__ const V2<Rl> *in(int) const { return data; }
@@ -46,21 +54,36 @@ template <class Rl> struct NlsRow {
         V2<Rl>(&v)[P] = vv[0];
         const Sm &sm = smm[0];
         V2<Rl> *p = data + row * N;
-        block_fft<N, P, +1, BLOCK>(v, sm, t, tw);
-        fence(v);
+        auto nonlinear = [&]() {
 #pragma unroll
-        for (int m = 0; m < P; ++m) {
-            // psi exp(-i th) = psi + psi (cos th - 1 - i sin th): the
-            // increment is formed without cancellation, so the modulus is
-            // kept to the final rounding
-            const Rl x = v[m].x, y = v[m].y;
-            Rl sn, cm1;
-            phase_terms(sigma_dt * (x * x + y * y), sn, cm1);
-            v[m].x = x + (x * cm1 + y * sn);
-            v[m].y = y + (y * cm1 - x * sn);
+            for (int m = 0; m < P; ++m) {
+                // psi exp(-i th) = psi + psi (cos th - 1 - i sin th): the
+                // increment is formed without cancellation, so the modulus is
+                // kept to the final rounding
+                const Rl x = v[m].x, y = v[m].y;
+                Rl sn, cm1;
+                phase_terms(sigma_dt * (x * x + y * y), sn, cm1);
+                v[m].x = x + (x * cm1 + y * sn);
+                v[m].y = y + (y * cm1 - x * sn);
+            }
+        };
+        if constexpr (PSS_SHARED_FFT && sizeof(Rl) == 4) {
+            conj_all(v);
+#pragma unroll 1
+            for (int pass = 0; pass < 2; ++pass) {
+                block_fft<N, P, -1, BLOCK>(v, sm, t, tw);
+                if (pass == 0) {
+                    conj_all(v);
+                    nonlinear();
+                }
+            }
+        } else {
+            block_fft<N, P, +1, BLOCK>(v, sm, t, tw);
+            fence(v);
+            nonlinear();
+            fence(v);
+            block_fft<N, P, -1, BLOCK>(v, sm, t, tw);
         }
-        fence(v);
-        block_fft<N, P, -1, BLOCK>(v, sm, t, tw);
         store_line<P, T>(v, p, 1, t, ok);
     }
 };
@@ -78,6 +101,8 @@ template <class V, class W> __device__ __forceinline__ V apply_km1(V z, W km1)
 
 template <class Rl> struct NlsCol {
     static constexpr int NIN = 1;
+    static constexpr bool LEAN = true;
+    static constexpr int PMAX = 32;
     V2<Rl> *data;
     int64_t nx;
     Rl scale;
@@ -91,18 +116,33 @@ template <class Rl> struct NlsCol {
         V2<Rl>(&v)[P] = vv[0];
         const Sm &sm = smm[0];
         V2<Rl> *p = data + field * N * nx + x;
-        block_fft<N, P, -1, BLOCK>(v, sm, t, tw);
-        fence(v);
-        const TW<Rl> a = __ldg(ax + x);
-        const TW<Rl> *byl = launder(by);  // keep these loads after the transform
+        auto propagate = [&]() {
+            const TW<Rl> a = __ldg(ax + x);
+            const TW<Rl> *byl = launder(by);  // keep these loads after the transform
 #pragma unroll
-        for (int m = 0; m < P; ++m) {
-            // scale is a power of two: exact
-            const V2<Rl> z = apply_km1(cscale(v[m], scale), a);
-            v[m] = apply_km1(z, __ldg(byl + t + T * m));
+            for (int m = 0; m < P; ++m) {
+                // scale is a power of two: exact
+                const V2<Rl> z = apply_km1(cscale(v[m], scale), a);
+                v[m] = apply_km1(z, __ldg(byl + t + T * m));
+            }
+        };
+        if constexpr (PSS_SHARED_FFT && sizeof(Rl) == 4) {
+#pragma unroll 1
+            for (int pass = 0; pass < 2; ++pass) {
+                block_fft<N, P, -1, BLOCK>(v, sm, t, tw);
+                if (pass == 0) {
+                    propagate();
+                    conj_all(v);
+                }
+            }
+            conj_all(v);
+        } else {
+            block_fft<N, P, -1, BLOCK>(v, sm, t, tw);
+            fence(v);
+            propagate();
+            fence(v);
+            block_fft<N, P, +1, BLOCK>(v, sm, t, tw);
         }
-        fence(v);
-        block_fft<N, P, +1, BLOCK>(v, sm, t, tw);
         store_line<P, T>(v, p, nx, t, true);
     }
 };

@@ -24,6 +24,15 @@
 
 namespace pss {
 
+// NS passes hold two arrays of P points per thread: with 16 points they fit
+// without spills in the double-buffered shape (the lean shape would spill)
+#ifndef NS_PMAX
+#define NS_PMAX 16
+#endif
+#ifndef NS_LEAN
+#define NS_LEAN false
+#endif
+
 struct NsField {
     int idx;        // buffer holding w^n
     int active;     // still iterating in this step
@@ -49,6 +58,8 @@ template <class V, class R> __device__ __forceinline__ void ns_derivs(V w, R kx,
 
 template <class Rl> struct NsRow {
     static constexpr int NIN = 2;
+    static constexpr bool LEAN = NS_LEAN;
+    static constexpr int PMAX = NS_PMAX;
     V2<Rl> *c1, *c2;  // in: C1, C2 rows; out: row transform of J into c1
     const NsField *fs;
     int64_t ny;
@@ -72,6 +83,8 @@ template <class Rl> struct NsRow {
 
 template <class Rl> struct NsCol {
     static constexpr int NIN = 1;
+    static constexpr bool LEAN = NS_LEAN;
+    static constexpr int PMAX = NS_PMAX;
     V2<Rl> *c1, *c2;        // in: J row transforms (c1); out: C1, C2 of w^{k+1}
     V2<Rl> *w0, *w1, *w2;   // vorticity buffers
     V2<Rl> *jn;             // J_hat^n (written when k == 0)
@@ -159,6 +172,8 @@ template <class Rl> struct NsCol {
 // after set_state, before the first row pass
 template <class Rl> struct NsPrep {
     static constexpr int NIN = 1;
+    static constexpr bool LEAN = NS_LEAN;
+    static constexpr int PMAX = NS_PMAX;
     const V2<Rl> *w;
     V2<Rl> *c1, *c2;
     const Rl *kxo, *kyo, *kx2, *ky2;
@@ -255,8 +270,8 @@ cudaError_t ns_col_pass(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, 
     switch (ny) {
 #define PSS_CASE(N)                                         \
     case N:                                                 \
-        op.W = ColCfg<Rl, N, 1>::W;                         \
-        *groups_out = int(nx / ColCfg<Rl, N, 1>::W);        \
+        op.W = ColCfgOf<Rl, N, NsCol<Rl>>::W;                         \
+        *groups_out = int(nx / ColCfgOf<Rl, N, NsCol<Rl>>::W);        \
         return launch_col_n<Rl, N>(op, twy, nx, batch, s);
         PSS_FOR_EACH_N(PSS_CASE)
 #undef PSS_CASE

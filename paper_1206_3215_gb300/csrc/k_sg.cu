@@ -23,9 +23,18 @@ namespace pss {
 
 __device__ __forceinline__ float sin_(float a) { return sinf(a); }
 __device__ __forceinline__ double sin_(double a) { return sin(a); }
+// correctly rounded reciprocal
+__device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double rcp_(double a) { return __drcp_rn(a); }
+
+// FP32: both transforms of a pass run through one forward-FFT body
+// (F^-1 x = conj(F conj x)), which keeps the pass within 128 registers.
+constexpr bool sg_shared(int bytes) { return bytes == 4; }
 
 template <class Rl> struct SgRow {
     static constexpr int NIN = 1;
+    static constexpr bool LEAN = sg_shared(sizeof(Rl));
+    static constexpr int PMAX = 32;
     V2<Rl> *h;  // in: H rows; out: S rows (in place)
     __device__ const V2<Rl> *in(int) const { return h; }
     template <int N, int P, bool BLOCK, class Sm>
@@ -33,18 +42,31 @@ template <class Rl> struct SgRow {
                                         const TW<Rl> *tw) const
     {
         V2<Rl>(&v)[P] = vv[0];
-        block_fft<N, P, +1, BLOCK>(v, sm[0], t, tw);
-        fence(v);
+        if constexpr (sg_shared(sizeof(Rl))) {
+            conj_all(v);
+#pragma unroll 1
+            for (int pass = 0; pass < 2; ++pass) {
+                block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw);
+                if (pass == 0)  // u = Re F^-1 H = Re conj(F conj H) = Re F conj H
 #pragma unroll
-        for (int m = 0; m < P; ++m) v[m] = V2<Rl>{sin_(v[m].x), Rl(0)};
-        fence(v);
-        block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw);
+                    for (int m = 0; m < P; ++m) v[m] = V2<Rl>{sin_(v[m].x), Rl(0)};
+            }
+        } else {
+            block_fft<N, P, +1, BLOCK>(v, sm[0], t, tw);
+            fence(v);
+#pragma unroll
+            for (int m = 0; m < P; ++m) v[m] = V2<Rl>{sin_(v[m].x), Rl(0)};
+            fence(v);
+            block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw);
+        }
         store_line<P, N / P>(v, h + r * N, 1, t, ok);
     }
 };
 
 template <class Rl> struct SgCol {
     static constexpr int NIN = 1;
+    static constexpr bool LEAN = sg_shared(sizeof(Rl));
+    static constexpr int PMAX = 32;
     V2<Rl> *h;          // in: S columns; out: next H
     V2<Rl> *u, *d;      // uhat^n, d^n, updated in place
     const Rl *kx2, *ky2;
@@ -58,24 +80,44 @@ template <class Rl> struct SgCol {
         constexpr int T = N / P;
         V2<Rl>(&v)[P] = vv[0];
         const int64_t base = field * N * nx + x;
-        block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw);
-        fence(v);
-        const Rl kx = __ldg(kx2 + x);
+        auto update = [&]() {
+            const Rl kx = __ldg(kx2 + x);
+            // one running pointer per array (T rows apart), so the 2P loads and
+            // stores do not each hold a 64-bit address
+            const int64_t step = int64_t(T) * nx;
+            V2<Rl> *pu = u + base + int64_t(t) * nx, *pd = d + base + int64_t(t) * nx;
 #pragma unroll
-        for (int m = 0; m < P; ++m) {
-            const int y = t + T * m;
-            const int64_t i = base + int64_t(y) * nx;
-            const V2<Rl> un = u[i], dn = d[i];
-            const Rl a = dt2 * (kx + __ldg(ky2 + y));
-            const Rl inv = Rl(1) / (Rl(1) + Rl(0.25) * a);
-            const V2<Rl> dn1{dn.x - (a * un.x + dt2 * v[m].x) * inv, dn.y - (a * un.y + dt2 * v[m].y) * inv};
-            const V2<Rl> un1{un.x + dn1.x, un.y + dn1.y};
-            d[i] = dn1;
-            u[i] = un1;
-            v[m] = cscale(un1, inv_n2);
+            for (int m = 0; m < P; ++m) {
+                const int y = t + T * m;
+                const V2<Rl> un = *pu, dn = *pd;
+                const Rl a = dt2 * (kx + __ldg(ky2 + y));
+                const Rl inv = rcp_(Rl(1) + Rl(0.25) * a);
+                const V2<Rl> dn1{dn.x - (a * un.x + dt2 * v[m].x) * inv, dn.y - (a * un.y + dt2 * v[m].y) * inv};
+                const V2<Rl> un1{un.x + dn1.x, un.y + dn1.y};
+                *pd = dn1;
+                *pu = un1;
+                v[m] = cscale(un1, inv_n2);
+                pu += step;
+                pd += step;
+            }
+        };
+        if constexpr (sg_shared(sizeof(Rl))) {
+#pragma unroll 1
+            for (int pass = 0; pass < 2; ++pass) {
+                block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw);
+                if (pass == 0) {
+                    update();
+                    conj_all(v);
+                }
+            }
+            conj_all(v);
+        } else {
+            block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw);
+            fence(v);
+            update();
+            fence(v);
+            block_fft<N, P, +1, BLOCK>(v, sm[0], t, tw);
         }
-        fence(v);
-        block_fft<N, P, +1, BLOCK>(v, sm[0], t, tw);
         store_line<P, T>(v, h + base, nx, t, true);
     }
 };

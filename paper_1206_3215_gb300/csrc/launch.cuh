@@ -51,7 +51,7 @@ template <class K> inline cudaError_t resident_ctas(K kernel, int threads, size_
 template <class Rl, int N, class Op>
 inline cudaError_t launch_row_n(Op op, const TW<Rl> *tw, int64_t rows_total, cudaStream_t s)
 {
-    using C = RowCfg<Rl, N, Op::NIN>;
+    using C = RowCfgOf<Rl, N, Op>;
     auto k = k_row<Rl, N, Op>;
     static std::atomic<unsigned> done{0};
     static int ctas[32] = {};
@@ -69,7 +69,7 @@ inline cudaError_t launch_row_n(Op op, const TW<Rl> *tw, int64_t rows_total, cud
 template <class Rl, int N, class Op>
 inline cudaError_t launch_col_n(Op op, const TW<Rl> *tw, int64_t nx, int64_t batch, cudaStream_t s)
 {
-    using C = ColCfg<Rl, N, Op::NIN>;
+    using C = ColCfgOf<Rl, N, Op>;
     auto k = k_col<Rl, N, Op>;
     static std::atomic<unsigned> done{0};
     static int ctas[32] = {};

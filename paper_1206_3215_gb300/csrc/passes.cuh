@@ -46,29 +46,36 @@ namespace pss {
 #ifndef PSS_COL_THREADS
 #define PSS_COL_THREADS 256
 #endif
+// FP32 (measured, 1024^2): one shared-memory buffer per CTA and two CTAs per
+// SM (<= 128 registers) beat a double-buffered CTA alone by 9 %; FP64 keeps
+// the double buffer and one CTA per SM.
 #ifndef PSS_MIN_CTAS
-#define PSS_MIN_CTAS 1
+#define PSS_MIN_CTAS 2
+#endif
+#ifndef PSS_MAX_NBUF
+#define PSS_MAX_NBUF 1
+#endif
+#ifndef PSS_MIN_CTAS64
+#define PSS_MIN_CTAS64 1
+#endif
+#ifndef PSS_MAX_NBUF64
+#define PSS_MAX_NBUF64 2
 #endif
 template <class Rl> struct Shape {
     static constexpr int ESZ = 2 * int(sizeof(Rl));
+    static constexpr int MIN_CTAS = sizeof(Rl) == 4 ? PSS_MIN_CTAS : PSS_MIN_CTAS64;
+    static constexpr int MAX_NBUF = sizeof(Rl) == 4 ? PSS_MAX_NBUF : PSS_MAX_NBUF64;
     // points per thread of the row and column transforms
     static constexpr int RP = sizeof(Rl) == 4 ? PSS_ROW_P : PSS_ROW_P64;
     static constexpr int CP = sizeof(Rl) == 4 ? PSS_COL_P : PSS_COL_P64;
     __host__ __device__ static constexpr int rowP(int n) { return n < RP ? n : RP; }
     __host__ __device__ static constexpr int colP(int n) { return n < CP ? n : CP; }
-    // rows per tile: about PSS_ROW_THREADS threads per CTA
-    __host__ __device__ static constexpr int rows(int n)
-    {
-        return (n / rowP(n)) >= PSS_ROW_THREADS ? 1 : PSS_ROW_THREADS / (n / rowP(n));
-    }
     // columns per tile: 64-byte row segments (FP32) when the thread budget
     // and shared memory (two buffers) allow
-    __host__ __device__ static constexpr int cols(int n)
+    __host__ __device__ static constexpr int cols(int n, int p)
     {
         int w = sizeof(Rl) == 4 ? 8 : 4;
-        while (w > 1 && ((long)2 * w * (n + n / 16) * ESZ > 200 * 1024L ||
-                         w * (n / colP(n)) > PSS_COL_THREADS))
-            w /= 2;
+        while (w > 1 && ((long)2 * w * (n + n / 16) * ESZ > 200 * 1024L || w * (n / p) > PSS_COL_THREADS)) w /= 2;
         return w;
     }
 };
@@ -103,28 +110,41 @@ __host__ __device__ constexpr int col_stride(int base, int W, int ESZ)
     return best;
 }
 
-template <class Rl, int N, int NIN> struct RowCfg {
-    static constexpr int P = Shape<Rl>::rowP(N), T = N / P, ROWS = Shape<Rl>::rows(N);
+// LEAN: one shared-memory buffer and (FP32) two resident CTAs per SM, for ops
+// whose transforms fit in 128 registers; otherwise a double buffer, one CTA.
+template <class Rl, int N, int NIN, bool LEAN = false, int PMAX = 32> struct RowCfg {
+    static constexpr int P = Shape<Rl>::rowP(N) < PMAX ? Shape<Rl>::rowP(N) : PMAX;
+    static constexpr int T = N / P;
+    static constexpr int ROWS = T >= PSS_ROW_THREADS ? 1 : PSS_ROW_THREADS / T;  // ~256 threads per CTA
     static constexpr int PADLOG = pad_log(P);
     static constexpr int LINE = N + (N >> PADLOG);
     static constexpr int THREADS = ROWS * T;
     static constexpr bool BLOCK = T > 32;
     // two buffers of NIN input lines per row (one when two do not fit)
     static constexpr int BUF = NIN * ROWS * LINE;
-    static constexpr int NBUF = size_t(2) * BUF * Shape<Rl>::ESZ <= SMEM_LIMIT ? 2 : 1;
+    static constexpr int MAXB = LEAN ? Shape<Rl>::MAX_NBUF : 2;
+    static constexpr int NBUF = (MAXB > 1 && size_t(2) * BUF * Shape<Rl>::ESZ <= SMEM_LIMIT) ? 2 : 1;
     static constexpr size_t SMEM = size_t(NBUF) * BUF * Shape<Rl>::ESZ;
+    static constexpr int MIN_CTAS = LEAN ? Shape<Rl>::MIN_CTAS : 1;
 };
 
-template <class Rl, int N, int NIN> struct ColCfg {
-    static constexpr int P = Shape<Rl>::colP(N), T = N / P, W = Shape<Rl>::cols(N);
+template <class Rl, int N, int NIN, bool LEAN = false, int PMAX = 32> struct ColCfg {
+    static constexpr int P = Shape<Rl>::colP(N) < PMAX ? Shape<Rl>::colP(N) : PMAX;
+    static constexpr int T = N / P;
+    static constexpr int W = Shape<Rl>::cols(N, P);
     static constexpr int PADLOG = pad_log(P);
     static constexpr int STRIDE = col_stride(N + (N >> PADLOG), W, Shape<Rl>::ESZ);
     static constexpr int THREADS = W * T;
     static constexpr bool BLOCK = THREADS > 32;
     static constexpr int BUF = NIN * W * STRIDE;
-    static constexpr int NBUF = size_t(2) * BUF * Shape<Rl>::ESZ <= SMEM_LIMIT ? 2 : 1;
+    static constexpr int MAXB = LEAN ? Shape<Rl>::MAX_NBUF : 2;
+    static constexpr int NBUF = (MAXB > 1 && size_t(2) * BUF * Shape<Rl>::ESZ <= SMEM_LIMIT) ? 2 : 1;
     static constexpr size_t SMEM = size_t(NBUF) * BUF * Shape<Rl>::ESZ;
+    static constexpr int MIN_CTAS = LEAN ? Shape<Rl>::MIN_CTAS : 1;
 };
+
+template <class Rl, int N, class Op> using RowCfgOf = RowCfg<Rl, N, Op::NIN, Op::LEAN, Op::PMAX>;
+template <class Rl, int N, class Op> using ColCfgOf = ColCfg<Rl, N, Op::NIN, Op::LEAN, Op::PMAX>;
 
 // ----------------------------------------------------------------------------
 // cp.async: per-thread asynchronous global -> shared copies (no registers held)
@@ -149,8 +169,10 @@ template <int N> __device__ __forceinline__ void cp_async_wait()
 template <int P, int T, class V, class Sm>
 __device__ __forceinline__ void stage_line(const Sm &sm, const V *__restrict__ src, int64_t st, int t)
 {
+    const V *p = src + int64_t(t) * st;  // running pointer: one live address
+    const int64_t step = int64_t(T) * st;
 #pragma unroll
-    for (int m = 0; m < P; ++m) cp_async<sizeof(V)>(&sm[t + T * m], src + int64_t(t + T * m) * st);
+    for (int m = 0; m < P; ++m, p += step) cp_async<sizeof(V)>(&sm[t + T * m], p);
 }
 template <int P, int T, class V, class Sm>
 __device__ __forceinline__ void read_line(V (&v)[P], const Sm &sm, int t)
@@ -164,10 +186,10 @@ __device__ __forceinline__ void read_line(V (&v)[P], const Sm &sm, int t)
 
 // rows_total = batch * ny; row r of the batch starts at element r * NX
 template <class Rl, int N, class Op>
-__global__ void __launch_bounds__(RowCfg<Rl, N, Op::NIN>::THREADS, PSS_MIN_CTAS)
+__global__ void __launch_bounds__(RowCfgOf<Rl, N, Op>::THREADS, RowCfgOf<Rl, N, Op>::MIN_CTAS)
     k_row(Op op, const TW<Rl> *__restrict__ tw, int64_t rows_total)
 {
-    using C = RowCfg<Rl, N, Op::NIN>;
+    using C = RowCfgOf<Rl, N, Op>;
     using V = V2<Rl>;
     using Sm = SmemLine<V, C::PADLOG>;
     constexpr int NIN = Op::NIN;
@@ -213,10 +235,10 @@ __global__ void __launch_bounds__(RowCfg<Rl, N, Op::NIN>::THREADS, PSS_MIN_CTAS)
 
 // tiles: (NX / W) column groups per field, fields in order
 template <class Rl, int N, class Op>
-__global__ void __launch_bounds__(ColCfg<Rl, N, Op::NIN>::THREADS, PSS_MIN_CTAS)
+__global__ void __launch_bounds__(ColCfgOf<Rl, N, Op>::THREADS, ColCfgOf<Rl, N, Op>::MIN_CTAS)
     k_col(Op op, const TW<Rl> *__restrict__ tw, int64_t nx, int64_t batch)
 {
-    using C = ColCfg<Rl, N, Op::NIN>;
+    using C = ColCfgOf<Rl, N, Op>;
     using V = V2<Rl>;
     using Sm = SmemLine<V, C::PADLOG>;
     constexpr int NIN = Op::NIN;
@@ -270,8 +292,10 @@ __device__ __forceinline__ void store_line(const V (&v)[P], V *__restrict__ p, i
                                            bool ok)
 {
     if (!ok) return;
+    V *q = p + int64_t(t) * st;  // running pointer: one live address
+    const int64_t step = int64_t(T) * st;
 #pragma unroll
-    for (int m = 0; m < P; ++m) p[int64_t(t + T * m) * st] = v[m];
+    for (int m = 0; m < P; ++m, q += step) *q = v[m];
 }
 
 // ----------------------------------------------------------------------------
@@ -279,6 +303,8 @@ __device__ __forceinline__ void store_line(const V (&v)[P], V *__restrict__ p, i
 
 template <class Rl, int DIR> struct RowFft {
     static constexpr int NIN = 1;
+    static constexpr bool LEAN = true;
+    static constexpr int PMAX = 32;
     V2<Rl> *data;
     Rl scale;  // applied after the transform when != 1
     __device__ const V2<Rl> *in(int) const { return data; }
@@ -296,6 +322,8 @@ template <class Rl, int DIR> struct RowFft {
 
 template <class Rl, int DIR> struct ColFft {
     static constexpr int NIN = 1;
+    static constexpr bool LEAN = true;
+    static constexpr int PMAX = 32;
     V2<Rl> *data;
     int64_t nx;
     Rl scale;
