@@ -65,6 +65,7 @@ def _load():
                 "orc_ns_init": [P, L, L, I, P],
                 "orc_ns_jacobian": [P, L, L, D, D, P],
                 "orc_ns_run": [P, L, L, D, D, D, D, D, L, I, L, P],
+                "orc_ns_run_scheme": [P, L, L, D, D, D, D, D, L, I, L, P, I],
                 "orc_ns_field": [P, L, L, P],
                 "orc_ns_invariants": [P, L, L, D, D, P, P, P],
                 "orc_num_threads": [],
@@ -220,13 +221,16 @@ def ns_jacobian(what, lx: float, ly: float) -> np.ndarray:
 
 
 def ns_run(what, lx: float, ly: float, nu: float, dt: float, nsteps: int, tol: float = 1e-10,
-           max_iter: int = 100, dealias: bool = True):
-    """Returns (what_new, iterations per step, converged)."""
+           max_iter: int = 100, dealias: bool = True, scheme: str = "cn"):
+    """Returns (what_new, iterations per step, converged).  scheme "cn": the
+    paper's Crank-Nicolson with the trapezoidal Jacobian; "midpoint": implicit
+    midpoint (Jacobian of the mean of the iterate and w^n)."""
     a = _c128(what)
     ny, nx = a.shape
     iters = np.zeros(max(nsteps, 1), dtype=np.int64)
-    rc = _check(_load().orc_ns_run(_ptr(a), nx, ny, lx, ly, nu, dt, tol, max_iter,
-                                   int(dealias), nsteps, _ptr(iters)), "ns_run")
+    rc = _check(_load().orc_ns_run_scheme(_ptr(a), nx, ny, lx, ly, nu, dt, tol, max_iter,
+                                          int(dealias), nsteps, _ptr(iters),
+                                          {"cn": 0, "midpoint": 1}[scheme]), "ns_run")
     return a, iters[:nsteps], rc == 0
 
 

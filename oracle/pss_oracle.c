@@ -473,6 +473,16 @@ static void ns_jacobian_hat(const cplx *what, long nx, long ny, const double *kx
 int orc_ns_run(cplx *what, long nx, long ny, double lx, double ly, double nu, double dt,
                double tol, long max_iter, int dealias, long nsteps, long *iters)
 {
+    return orc_ns_run_scheme(what, nx, ny, lx, ly, nu, dt, tol, max_iter, dealias, nsteps, iters, 0);
+}
+
+/* scheme 0: the paper's Crank-Nicolson diffusion with the trapezoidal
+ * Jacobian (J^k + J^n)/2; scheme 1: implicit midpoint, the Jacobian of the
+ * midpoint (w^k + w^n)/2 with the same Crank-Nicolson diffusion:
+ *   (w^{k+1} - w^n)/dt - nu Lap (w^{k+1} + w^n)/2 + J((w^k + w^n)/2) = 0. */
+int orc_ns_run_scheme(cplx *what, long nx, long ny, double lx, double ly, double nu, double dt,
+                      double tol, long max_iter, int dealias, long nsteps, long *iters, int scheme)
+{
     if (!is_pow2(nx) || !is_pow2(ny) || nsteps < 0 || max_iter < 1) return -1;
     long n = nx * ny;
     double *kx = (double *)malloc(sizeof(double) * (size_t)nx);
@@ -496,16 +506,24 @@ int orc_ns_run(cplx *what, long nx, long ny, double lx, double ly, double nu, do
         while (k < max_iter) {
             const cplx *jcur = jn;
             if (k > 0) {
-                ns_jacobian_hat(wk, nx, ny, kx, ky, dealias, jk, J, d);
+                if (scheme == 1) {
+                    /* the midpoint (w^k + w^n)/2 */
+                    for (long i = 0; i < n; i++) wk1[i] = 0.5 * (wk[i] + what[i]);
+                    ns_jacobian_hat(wk1, nx, ny, kx, ky, dealias, jk, J, d);
+                } else {
+                    ns_jacobian_hat(wk, nx, ny, kx, ky, dealias, jk, J, d);
+                }
                 jcur = jk;
             }
-            /* (w^{k+1} - w^n)/dt - nu Lap (w^{k+1} + w^n)/2 + (J^k + J^n)/2 = 0 */
             ksum diff = {0, 0};
             for (long y = 0; y < ny; y++)
                 for (long x = 0; x < nx; x++) {
                     long i = y * nx + x;
                     double a = 0.5 * dt * nu * (kx[x] * kx[x] + ky[y] * ky[y]);
-                    wk1[i] = ((1.0 - a) * what[i] - 0.5 * dt * (jcur[i] + jn[i])) / (1.0 + a);
+                    if (scheme == 1) /* ... + J((w^k + w^n)/2) = 0 */
+                        wk1[i] = ((1.0 - a) * what[i] - dt * jcur[i]) / (1.0 + a);
+                    else /* ... + (J^k + J^n)/2 = 0 */
+                        wk1[i] = ((1.0 - a) * what[i] - 0.5 * dt * (jcur[i] + jn[i])) / (1.0 + a);
                     cplx e = wk1[i] - wk[i];
                     ks_add(&diff, creal(e) * creal(e) + cimag(e) * cimag(e));
                 }

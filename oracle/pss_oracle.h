@@ -58,6 +58,10 @@ int orc_ns_jacobian(const double complex *what, long nx, long ny, double lx, dou
  * iters[s] (if non-NULL, length nsteps) receives the number of CN updates of step s. */
 int orc_ns_run(double complex *what, long nx, long ny, double lx, double ly, double nu,
                double dt, double tol, long max_iter, int dealias, long nsteps, long *iters);
+/* scheme 0 as above; scheme 1: implicit midpoint (Jacobian of (w^k + w^n)/2) */
+int orc_ns_run_scheme(double complex *what, long nx, long ny, double lx, double ly, double nu,
+                      double dt, double tol, long max_iter, int dealias, long nsteps, long *iters,
+                      int scheme);
 int orc_ns_field(const double complex *what, long nx, long ny, double *w);
 /* circulation = integral w, enstrophy = integral w^2 / 2, energy = integral |u|^2 / 2 */
 int orc_ns_invariants(const double complex *what, long nx, long ny, double lx, double ly,

@@ -120,3 +120,30 @@ def test_non_convergence_is_reported(orc):
     wh = orc.ns_init(S.ns_power_law(n), dealias=True)
     _, iters, ok = orc.ns_run(wh, L, L, 1e-3, 2.5e-3, 3, max_iter=1)
     assert not ok and (iters == 1).all()
+
+
+def test_midpoint_equals_cn_when_j_vanishes(orc):
+    # Taylor-Green: J = 0, both schemes reduce to the same CN amplification
+    g = _golden("ns_taylor_green_table4.txt")
+    n = 32
+    wh = orc.ns_init(S.taylor_green_paper(n), dealias=False)
+    a, _, _ = orc.ns_run(wh, 1.0, 1.0, g["nu"], g["dt"], 20, dealias=False, scheme="cn")
+    b, _, _ = orc.ns_run(wh, 1.0, 1.0, g["nu"], g["dt"], 20, dealias=False, scheme="midpoint")
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+
+
+def test_midpoint_conserves_quadratic_invariants_inviscid(orc):
+    # nu = 0 with the 2/3 rule: the truncated Jacobian conserves energy and
+    # enstrophy exactly, and the implicit midpoint rule keeps every quadratic
+    # invariant of the ODE; only the fixed-point tolerance is left
+    n, L, dt = 64, 2 * math.pi, 1e-2
+    wh = orc.ns_init(S.ns_power_law(n), dealias=True)
+    c0, z0, e0 = orc.ns_invariants(wh, L, L)
+    w1, iters, ok = orc.ns_run(wh, L, L, 0.0, dt, 20, tol=1e-24, max_iter=200, scheme="midpoint")
+    assert ok
+    c1, z1, e1 = orc.ns_invariants(w1, L, L)
+    assert abs(z1 - z0) / z0 <= 1e-12 and abs(e1 - e0) / e0 <= 1e-12
+    # the trapezoidal (paper) scheme does not conserve them exactly
+    w2, _, _ = orc.ns_run(wh, L, L, 0.0, dt, 20, tol=1e-24, max_iter=200, scheme="cn")
+    c2, z2, e2 = orc.ns_invariants(w2, L, L)
+    assert abs(z2 - z0) / z0 > 1e-9
