@@ -66,6 +66,13 @@ extern "C" {
 #define PSS_FP32 0
 #define PSS_FP64 1
 
+/* Navier-Stokes time discretisations (pss_params.scheme) */
+#define PSS_NS_CN 0       /* Crank-Nicolson diffusion, trapezoidal Jacobian (J^k + J^n)/2,
+                             Section 4.3 (the default)                                   */
+#define PSS_NS_MIDPOINT 1 /* same diffusion, Jacobian of the midpoint (w^k + w^n)/2:
+                             the implicit midpoint rule, which keeps energy and
+                             enstrophy of the dealiased inviscid system exactly          */
+
 /* location of a caller buffer */
 #define PSS_HOST 0
 #define PSS_DEVICE 1
@@ -84,12 +91,15 @@ typedef struct pss_params {
     int32_t max_iter;  /* NS: bound on fixed-point updates per step (default 100)     */
     int32_t dealias;   /* NS: 1 = 2/3-rule square truncation (3|m| < n) on J and w0   */
     void *stream;      /* cudaStream_t to enqueue on, or NULL for a library stream    */
+    int32_t scheme;    /* NS: PSS_NS_CN or PSS_NS_MIDPOINT                             */
+    int32_t reserved;  /* must be 0                                                    */
 } pss_params;
 
 typedef struct pss_grid pss_grid;
 
 /* Fill *p with defaults: NLS, FP32, 64x64, batch 1, box [-10pi,10pi)^2,
- * dt 1e-3, sigma +1, nu 1/10, tol 1e-10, max_iter 100, dealias 1. */
+ * dt 1e-3, sigma +1, nu 1/10, tol 1e-10, max_iter 100, dealias 1,
+ * scheme PSS_NS_CN. */
 void pss_default_params(pss_params *p);
 
 /* Create a grid: validates *p, allocates every device buffer the equation

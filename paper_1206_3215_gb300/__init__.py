@@ -21,6 +21,7 @@ PSS_OK, PSS_E_ARG, PSS_E_OOM, PSS_E_CUDA, PSS_E_NOT_CONVERGED, PSS_E_NONFINITE, 
 PSS_EQ_NLS, PSS_EQ_SG, PSS_EQ_NS = 0, 1, 2
 PSS_FP32, PSS_FP64 = 0, 1
 PSS_HOST, PSS_DEVICE = 0, 1
+PSS_NS_CN, PSS_NS_MIDPOINT = 0, 1
 
 EXPORTED = [
     "pss_default_params", "pss_create_grid", "pss_set_state", "pss_step_n", "pss_get_state",
@@ -40,7 +41,7 @@ class PssParams(ctypes.Structure):
         ("lx", ctypes.c_double), ("ly", ctypes.c_double),
         ("dt", ctypes.c_double), ("sigma", ctypes.c_double), ("nu", ctypes.c_double),
         ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("dealias", ctypes.c_int32),
-        ("stream", ctypes.c_void_p),
+        ("stream", ctypes.c_void_p), ("scheme", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -225,6 +226,8 @@ class Grid:
         p = pss_default_params(eq=_EQ[eq], precision=PSS_FP32 if precision == "fp32" else PSS_FP64,
                                nx=nx, ny=ny, batch=batch)
         for k, v in params.items():
+            if k == "scheme" and isinstance(v, str):
+                v = {"cn": PSS_NS_CN, "midpoint": PSS_NS_MIDPOINT}[v]
             setattr(p, k, v)
         if stream is not None:
             p.stream = stream

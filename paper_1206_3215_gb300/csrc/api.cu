@@ -140,6 +140,8 @@ int pss_create_grid(pss_grid **out, const pss_params *p)
     else if (!(p->dt > 0) || !std::isfinite(p->dt)) bad = "dt";
     else if (!std::isfinite(p->sigma)) bad = "sigma";
     else if (p->eq == PSS_EQ_NS && (!(p->nu >= 0) || !(p->tol > 0) || p->max_iter < 1)) bad = "nu/tol/max_iter";
+    else if (p->scheme != PSS_NS_CN && p->scheme != PSS_NS_MIDPOINT) bad = "scheme";
+    else if (p->reserved != 0) bad = "reserved (must be 0)";
     if (bad) {
         g_create_error = std::string("invalid parameter: ") + bad;
         return PSS_E_ARG;

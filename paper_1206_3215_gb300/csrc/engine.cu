@@ -480,16 +480,41 @@ template <class Rl> int sg_conserved(pss_grid *g, double *out)
 
 namespace {
 
+// buffer i of field f
+template <class Rl> V2<Rl> *Bf(pss_grid *g, int i, int64_t f) { return B<Rl>(g, i) + f * g->npts; }
+
 template <class Rl> void ns_w(pss_grid *g, V2<Rl> *w[3])
 {
     for (int i = 0; i < 3; ++i) w[i] = B<Rl>(g, i);
 }
 
-template <class Rl> int ns_prep(pss_grid *g)
+// derivatives of w^n into C1, C2 (per_step: w^n of each field in its own
+// buffer idx; otherwise in buffer 0, as after set_state)
+template <class Rl> int ns_prep(pss_grid *g, bool per_step = false)
 {
-    return g->cuda(ns_prep_pass<Rl>(B<Rl>(g, 0), B<Rl>(g, 4), B<Rl>(g, 5), Rt<Rl>(g->kxo), Rt<Rl>(g->kyo),
-                                    Rt<Rl>(g->kx2), Rt<Rl>(g->ky2), g->nx, g->ny, g->batch, Tw<Rl>(g->twy),
-                                    g->stream), "ns derivatives");
+    V2<Rl> *w[3];
+    ns_w<Rl>(g, w);
+    return g->cuda(ns_prep_pass<Rl>(w, per_step ? g->ns_field : nullptr, B<Rl>(g, 4), B<Rl>(g, 5), Rt<Rl>(g->kxo),
+                                    Rt<Rl>(g->kyo), Rt<Rl>(g->kx2), Rt<Rl>(g->ky2), g->nx, g->ny, g->batch,
+                                    Tw<Rl>(g->twy), g->stream), "ns derivatives");
+}
+
+// derivatives of field f alone (its w^n in buffer 0)
+template <class Rl> int ns_prep_one(pss_grid *g, int64_t f)
+{
+    V2<Rl> *w[3] = {Bf<Rl>(g, 0, f), Bf<Rl>(g, 1, f), Bf<Rl>(g, 2, f)};
+    return g->cuda(ns_prep_pass<Rl>(w, nullptr, Bf<Rl>(g, 4, f), Bf<Rl>(g, 5, f), Rt<Rl>(g->kxo), Rt<Rl>(g->kyo),
+                                    Rt<Rl>(g->kx2), Rt<Rl>(g->ky2), g->nx, g->ny, 1, Tw<Rl>(g->twy), g->stream),
+                   "ns derivatives");
+}
+
+// start of a step: mark every field active; the midpoint scheme also needs
+// the derivatives of w^n (its last column pass wrote those of the midpoint)
+template <class Rl> int ns_step_begin(pss_grid *g)
+{
+    int rc = g->cuda(ns_begin(g->ns_field, g->batch, reinterpret_cast<int *>(g->flags), g->stream), "ns begin");
+    if (!rc && g->p.scheme == PSS_NS_MIDPOINT) rc = ns_prep<Rl>(g, true);
+    return rc;
 }
 
 template <class Rl> int ns_set(pss_grid *g, const void *w0, int where)
@@ -520,7 +545,8 @@ template <class Rl> int ns_update(pss_grid *g, bool in_graph)
     if (!in_graph && (rc = g->pass_begin(1))) return rc;
     e = ns_col_pass<Rl>(B<Rl>(g, 4), B<Rl>(g, 5), w, B<Rl>(g, 3), g->ns_field, g->partials, Rt<Rl>(g->kxo),
                         Rt<Rl>(g->kyo), Rt<Rl>(g->kx2), Rt<Rl>(g->ky2), Rt<Rl>(g->keepx), Rt<Rl>(g->keepy), g->p.dt,
-                        g->p.nu, g->nx, g->ny, g->batch, ctl, Tw<Rl>(g->twy), &groups, g->stream);
+                        g->p.nu, g->nx, g->ny, g->batch, ctl, g->p.scheme == PSS_NS_MIDPOINT ? 1 : 0, Tw<Rl>(g->twy),
+                        &groups, g->stream);
     if ((!in_graph && (rc = g->pass_end())) || (rc = g->cuda(e, "ns column pass"))) return rc;
     if (!in_graph && (rc = g->pass_begin(2))) return rc;
     e = ns_decide(g->ns_field, g->partials, groups, g->batch, ctl, parseval, g->p.tol, g->p.max_iter, g->stream);
@@ -529,10 +555,10 @@ template <class Rl> int ns_update(pss_grid *g, bool in_graph)
     return PSS_OK;
 }
 
-// One step as a graph: begin, then WHILE(some field active) { one update }.
+// One step as a graph: begin (and, midpoint scheme, the derivatives of w^n),
+// then WHILE(some field active) { one update }.
 template <class Rl> int ns_build_graph(pss_grid *g)
 {
-    int *ctl = reinterpret_cast<int *>(g->flags);
     cudaGraph_t graph = nullptr;
     int rc;
     if ((rc = g->cuda(cudaGraphCreate(&graph, 0), "graph create"))) return rc;
@@ -543,13 +569,19 @@ template <class Rl> int ns_build_graph(pss_grid *g)
     if ((rc = g->cuda(cudaStreamBeginCaptureToGraph(g->stream, graph, nullptr, nullptr, 0,
                                                     cudaStreamCaptureModeRelaxed), "capture")))
         return rc;
-    cudaError_t e = ns_begin(g->ns_field, g->batch, ctl, g->stream);
+    rc = ns_step_begin<Rl>(g);
+    // the last node captured so far: the WHILE node depends on it
+    cudaGraphNode_t begin_node = nullptr;
+    cudaStreamCaptureStatus status;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(g->stream, &status, nullptr, nullptr, &deps, nullptr, &ndeps);
+    if (e == cudaSuccess && ndeps == 1) begin_node = deps[0];
     cudaGraph_t out = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(g->stream, &out);
+    if (rc) return rc;
     if ((rc = g->cuda(e != cudaSuccess ? e : e2, "capture begin"))) return rc;
-    cudaGraphNode_t begin_node = nullptr;
-    size_t count = 1;
-    if ((rc = g->cuda(cudaGraphGetNodes(graph, &begin_node, &count), "graph nodes"))) return rc;
+    if (!begin_node) return g->fail(PSS_E_CUDA, "step graph: expected one node before the loop, found %zu", ndeps);
     // zero-initialised node parameters (the struct's union has no default constructor)
     alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
     cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(raw);
@@ -587,7 +619,7 @@ template <class Rl> int ns_step(pss_grid *g, int64_t n)
         return PSS_OK;  // a field that reached max_iter is reported by the next synchronising call
     }
     for (int64_t s = 0; s < n; ++s) {
-        if ((rc = g->cuda(ns_begin(g->ns_field, g->batch, ctl, g->stream), "ns begin"))) return rc;
+        if ((rc = ns_step_begin<Rl>(g))) return rc;
         for (int k = 0; k < g->p.max_iter; ++k) {
             if ((rc = ns_update<Rl>(g, false))) return rc;
             if ((rc = g->cuda(cudaMemcpyAsync(hctl, ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, g->stream),
@@ -648,8 +680,6 @@ template <class Rl> int ns_conserved(pss_grid *g, double *out)
 
 namespace {
 
-template <class Rl> V2<Rl> *Bf(pss_grid *g, int i, int64_t f) { return B<Rl>(g, i) + f * g->npts; }
-
 template <class Rl> cudaError_t fft2_one(pss_grid *g, V2<Rl> *b, int dir)
 {
     cudaError_t e = fft_rows<Rl>(b, g->nx, g->ny, dir, Rl(1), Tw<Rl>(g->twx), g->stream);
@@ -708,9 +738,7 @@ template <class Rl> int field_set(pss_grid *g, int64_t f, const void *a, const v
                                          g->stream), "mask")) ||
             (rc = g->cuda(cudaMemsetAsync(static_cast<char *>(g->ns_field) + f * ns_field_bytes(), 0, ns_field_bytes(),
                                           g->stream), "record")) ||
-            (rc = g->cuda(ns_prep_pass<Rl>(Bf<Rl>(g, 0, f), Bf<Rl>(g, 4, f), Bf<Rl>(g, 5, f), Rt<Rl>(g->kxo),
-                                           Rt<Rl>(g->kyo), Rt<Rl>(g->kx2), Rt<Rl>(g->ky2), g->nx, g->ny, 1,
-                                           Tw<Rl>(g->twy), g->stream), "ns derivatives")))
+            (rc = ns_prep_one<Rl>(g, f)))
             return rc;
     }
     return where == PSS_HOST ? g->cuda(cudaStreamSynchronize(g->stream), "sync") : PSS_OK;

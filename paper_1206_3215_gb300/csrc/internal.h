@@ -61,9 +61,9 @@ template <class Rl>
 cudaError_t ns_col_pass(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, void *fs, double *partials,
                         const Rl *kxo, const Rl *kyo, const Rl *kx2, const Rl *ky2, const Rl *keepx,
                         const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch,
-                        const int *ctl, const TW<Rl> *twy, int *groups_out, cudaStream_t s);
+                        const int *ctl, int midpoint, const TW<Rl> *twy, int *groups_out, cudaStream_t s);
 template <class Rl>
-cudaError_t ns_prep_pass(const V2<Rl> *w, V2<Rl> *c1, V2<Rl> *c2, const Rl *kxo, const Rl *kyo,
+cudaError_t ns_prep_pass(V2<Rl> *const w[3], const void *fs, V2<Rl> *c1, V2<Rl> *c2, const Rl *kxo, const Rl *kyo,
                          const Rl *kx2, const Rl *ky2, int64_t nx, int64_t ny, int64_t batch,
                          const TW<Rl> *twy, cudaStream_t s);
 // loop control ctl (4 ints on the device): [0] update index, [1] any field

@@ -1,0 +1,254 @@
+// Fused passes of the Navier-Stokes Crank-Nicolson / fixed-point scheme
+// (vorticity form, Section 3.3; time stepping, Section 4.3).
+//
+//   (w^{k+1} - w^n)/dt - nu Lap (w^{k+1} + w^n)/2 + (J^k + J^n)/2 = 0,
+//   J = psi_y w_x - psi_x w_y,  Lap psi = -w,
+// iterated over k until integral (w^{k+1} - w^k)^2 < tol.  The implicit
+// midpoint variant replaces (J^k + J^n)/2 by J^k_mid, the Jacobian of
+// (w^k + w^n)/2: the column pass then transforms the derivatives of that
+// midpoint instead of those of w^{k+1}, and J_hat^n is not kept.  Its first
+// update (w^0 = w^n) is the same as Crank-Nicolson's.
+//
+// The Jacobian needs four derivative fields; they are packed into two complex
+// fields whose transforms are
+//   C1 = psi_y - i psi_x  <->  (kx + i ky) psi_hat,
+//   C2 = w_x + i w_y      <->  i (kx + i ky) w_hat,
+// so that J = Re C1 Re C2 + Im C1 Im C2 pointwise.  One fixed-point update is
+// a row pass (row inverse transforms of C1 and C2, J, row forward transform)
+// and a column pass (column forward transform -> J_hat with the 2/3 mask, CN
+// update, FP64 partial of |w^{k+1} - w^k|^2, derivatives of w^{k+1}, column
+// inverse transforms into C1 and C2).  A small kernel then folds the partials
+// per field in a fixed order and decides, per field, whether to stop.
+//
+// Vorticity iterates live in three buffers per field: w^n in buffer idx, the
+// iterate of update k >= 1 in (idx + 1 + ((k - 1) & 1)) % 3.  Fields that have
+// converged skip their loads and stores while the others iterate, so a field
+// gets exactly the updates it would get alone.
+#pragma once
+#include "launch.cuh"
+
+namespace pss {
+
+// NS passes hold two arrays of P points per thread: with 16 points they fit
+// without spills in the double-buffered shape (the lean shape would spill)
+#ifndef NS_PMAX
+#define NS_PMAX 16
+#endif
+#ifndef NS_LEAN
+#define NS_LEAN false
+#endif
+
+struct NsField {
+    int idx;        // buffer holding w^n
+    int active;     // still iterating in this step
+    int nonconv;    // reached max_iter in some step (sticky)
+    int pad;
+    long long updates;  // CN updates (= Jacobian evaluations) summed over steps
+};
+
+__host__ __device__ __forceinline__ int ns_buf(int idx, int k)
+{
+    return k == 0 ? idx : (idx + 1 + ((k - 1) & 1)) % 3;
+}
+
+// packed derivative spectra of w_hat at wavenumber (kx, ky) (odd-derivative
+// wavenumbers: zero at the Nyquist index), times the inverse-transform scale
+template <class V, class R> __device__ __forceinline__ void ns_derivs(V w, R kx, R ky, R k2, R s, V &c1, V &c2)
+{
+    const R inv = k2 > R(0) ? s / k2 : R(0);
+    const V p{w.x * inv, w.y * inv};  // psi_hat * s
+    c1 = V{kx * p.x - ky * p.y, kx * p.y + ky * p.x};
+    c2 = V{-(kx * w.y + ky * w.x) * s, (kx * w.x - ky * w.y) * s};
+}
+
+template <class Rl> struct NsRow {
+    static constexpr int NIN = 2;
+    static constexpr bool LEAN = NS_LEAN;
+    static constexpr int PMAX = NS_PMAX;
+    V2<Rl> *c1, *c2;  // in: C1, C2 rows; out: row transform of J into c1
+    const NsField *fs;
+    int64_t ny;
+    __device__ const V2<Rl> *in(int k) const { return k == 0 ? c1 : c2; }
+    template <int N, int P, bool BLOCK, class Sm>
+    __device__ __forceinline__ void row(V2<Rl> (&v)[2][P], int64_t r, bool ok, int t, const Sm (&sm)[2],
+                                        const TW<Rl> *tw) const
+    {
+        block_fft<N, P, +1, BLOCK>(v[0], sm[0], t, tw);
+        block_fft<N, P, +1, BLOCK>(v[1], sm[1], t, tw);
+        fence(v[0]);
+        fence(v[1]);
+#pragma unroll
+        for (int m = 0; m < P; ++m) v[0][m] = V2<Rl>{v[0][m].x * v[1][m].x + v[0][m].y * v[1][m].y, Rl(0)};
+        fence(v[0]);
+        block_fft<N, P, -1, BLOCK>(v[0], sm[0], t, tw);
+        const bool live = ok && fs[r / ny].active;
+        store_line<P, N / P>(v[0], c1 + r * N, 1, t, live);
+    }
+};
+
+template <class Rl, bool MID> struct NsCol {
+    static constexpr int NIN = 1;
+    static constexpr bool LEAN = NS_LEAN;
+    static constexpr int PMAX = NS_PMAX;
+    V2<Rl> *c1, *c2;        // in: J row transforms (c1); out: C1, C2 of w^{k+1}
+    V2<Rl> *w0, *w1, *w2;   // vorticity buffers
+    V2<Rl> *jn;             // J_hat^n (written when k == 0)
+    NsField *fs;
+    double *partials;       // [field][column group]
+    const Rl *kxo, *kyo, *kx2, *ky2, *keepx, *keepy;
+    Rl half_dt, half_dt_nu, inv_n2;
+    int64_t nx;
+    const int *kptr;  // fixed-point update index of this pass (device, set by k_ns_advance)
+    int W;
+    static constexpr bool midpoint = MID;  // implicit midpoint, else trapezoidal Jacobian
+    __device__ const V2<Rl> *in(int) const { return c1; }
+    __device__ V2<Rl> *wb(int b) const { return b == 0 ? w0 : b == 1 ? w1 : w2; }
+    template <int N, int P, bool BLOCK, class Sm>
+    __device__ __forceinline__ void col(V2<Rl> (&vv)[1][P], int64_t field, int x, int t,
+                                        const Sm (&sm)[1], const TW<Rl> *tw) const
+    {
+        constexpr int T = N / P;
+        V2<Rl>(&v)[P] = vv[0];
+        const int k = *kptr;
+        const NsField f = fs[field];
+        const bool live = f.active != 0;
+        const int64_t base = field * N * nx + x;
+        const V2<Rl> *wn = wb(f.idx) + base;
+        const V2<Rl> *wk = wb(ns_buf(f.idx, k)) + base;
+        V2<Rl> *wk1 = wb(ns_buf(f.idx, k + 1)) + base;
+        block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw);
+        fence(v);
+        const Rl kx = __ldg(kxo + x), kxx = __ldg(kx2 + x), mx = __ldg(keepx + x);
+        double acc = 0.0;
+        V2<Rl> d2[P];
+#pragma unroll
+        for (int m = 0; m < P; ++m) {
+            const int y = t + T * m;
+            const int64_t o = int64_t(y) * nx;
+            const Rl mask = mx * __ldg(keepy + y);
+            const V2<Rl> jk{v[m].x * mask, v[m].y * mask};
+            // midpoint: jk is already J((w^k + w^n)/2), used twice below
+            V2<Rl> jnv = jk;
+            if constexpr (!MID) {
+                if (k == 0) {
+                    if (live) jn[base + o] = jk;
+                } else {
+                    jnv = live ? jn[base + o] : jk;
+                }
+            }
+            const V2<Rl> a_n = live ? wn[o] : V2<Rl>{0, 0};
+            const V2<Rl> a_k = live ? wk[o] : V2<Rl>{0, 0};
+            const Rl kk = kxx + __ldg(ky2 + y);
+            // w^{k+1} = [(1 - a) w^n - dt/2 (J^k + J^n)] / (1 + a), a = dt nu |k|^2 / 2,
+            // formed as w^n minus a small increment so that FP32 rounds the
+            // increment, not the nearly-unit decay factor, every step
+            const Rl a = half_dt_nu * kk;
+            const Rl inv = Rl(1) / (Rl(1) + a);
+            const V2<Rl> inc{(Rl(2) * a * a_n.x + half_dt * (jk.x + jnv.x)) * inv,
+                             (Rl(2) * a * a_n.y + half_dt * (jk.y + jnv.y)) * inv};
+            const V2<Rl> w1v{a_n.x - inc.x, a_n.y - inc.y};
+            const double ex = double(w1v.x) - double(a_k.x), ey = double(w1v.y) - double(a_k.y);
+            acc += ex * ex + ey * ey;
+            if (live) wk1[o] = w1v;
+            // field whose derivatives feed the next Jacobian: w^{k+1}, or the
+            // midpoint (w^{k+1} + w^n)/2 = w^n - inc/2
+            V2<Rl> wj = w1v;
+            if constexpr (MID) wj = V2<Rl>{a_n.x - Rl(0.5) * inc.x, a_n.y - Rl(0.5) * inc.y};
+            ns_derivs(wj, kx, __ldg(kyo + y), kk, inv_n2, v[m], d2[m]);
+        }
+        fence(v);
+        block_fft<N, P, +1, BLOCK>(v, sm[0], t, tw);
+        store_line<P, T>(v, c1 + base, nx, t, live);
+        block_fft<N, P, +1, BLOCK>(d2, sm[0], t, tw);
+        store_line<P, T>(d2, c2 + base, nx, t, live);
+        // FP64 partial of |w^{k+1} - w^k|^2 over this tile, folded in a fixed order
+        block_partial(acc, partials + field * (nx / W) + x / W);
+    }
+    // sum over the CTA (all threads of the tile) in a fixed tree; thread 0 writes
+    __device__ __forceinline__ void block_partial(double acc, double *out) const
+    {
+        __shared__ double red[32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        __syncthreads();
+        if (lane == 0) red[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int i = 0; i < int((blockDim.x + 31) >> 5); ++i) s += red[i];
+            *out = s;
+        }
+    }
+};
+
+// derivatives of w^n into C1, C2: the state after set_state (every field's
+// w^n in buffer 0: fs == nullptr), and, for the midpoint scheme, at the start
+// of every step (w^n in buffer fs[field].idx), since its last column pass
+// leaves the derivatives of the midpoint rather than those of w^{n+1}
+template <class Rl> struct NsPrep {
+    static constexpr int NIN = 1;
+    static constexpr bool LEAN = NS_LEAN;
+    static constexpr int PMAX = NS_PMAX;
+    const V2<Rl> *w0, *w1, *w2;
+    const NsField *fs;
+    V2<Rl> *c1, *c2;
+    const Rl *kxo, *kyo, *kx2, *ky2;
+    Rl inv_n2;
+    int64_t nx;
+    __device__ const V2<Rl> *in(int, int64_t field) const
+    {
+        const int b = fs ? fs[field].idx : 0;
+        return b == 0 ? w0 : b == 1 ? w1 : w2;
+    }
+    template <int N, int P, bool BLOCK, class Sm>
+    __device__ __forceinline__ void col(V2<Rl> (&vv)[1][P], int64_t field, int x, int t,
+                                        const Sm (&sm)[1], const TW<Rl> *tw) const
+    {
+        constexpr int T = N / P;
+        V2<Rl>(&v)[P] = vv[0];
+        const int64_t base = field * N * nx + x;
+        const Rl kx = __ldg(kxo + x), kxx = __ldg(kx2 + x);
+        V2<Rl> d2[P];
+#pragma unroll
+        for (int m = 0; m < P; ++m) {
+            const int y = t + T * m;
+            ns_derivs(v[m], kx, __ldg(kyo + y), kxx + __ldg(ky2 + y), inv_n2, v[m], d2[m]);
+        }
+        fence(v);
+        block_fft<N, P, +1, BLOCK>(v, sm[0], t, tw);
+        store_line<P, T>(v, c1 + base, nx, t, true);
+        block_fft<N, P, +1, BLOCK>(d2, sm[0], t, tw);
+        store_line<P, T>(d2, c2 + base, nx, t, true);
+    }
+};
+
+// column pass of one fixed-point update (scheme chosen by MID)
+template <class Rl, bool MID>
+cudaError_t ns_col_run(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, void *fs, double *partials,
+                        const Rl *kxo, const Rl *kyo, const Rl *kx2, const Rl *ky2, const Rl *keepx,
+                        const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch,
+                        const int *ctl, const TW<Rl> *twy, int *groups_out, cudaStream_t s)
+{
+    NsCol<Rl, MID> op{c1, c2, w[0], w[1], w[2], jn, static_cast<NsField *>(fs), partials, kxo, kyo, kx2, ky2,
+                 keepx, keepy, Rl(0.5 * dt), Rl(0.5 * dt * nu), Rl(1.0 / (double(nx) * double(ny))), nx, ctl, 0};
+    switch (ny) {
+#define PSS_CASE(N)                                         \
+    case N:                                                 \
+        op.W = ColCfgOf<Rl, N, NsCol<Rl, MID>>::W;                         \
+        *groups_out = int(nx / ColCfgOf<Rl, N, NsCol<Rl, MID>>::W);        \
+        return launch_col_n<Rl, N>(op, twy, nx, batch, s);
+        PSS_FOR_EACH_N(PSS_CASE)
+#undef PSS_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// the midpoint instantiations live in their own translation unit
+template <class Rl>
+cudaError_t ns_col_mid(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, void *fs, double *partials,
+                       const Rl *kxo, const Rl *kyo, const Rl *kx2, const Rl *ky2, const Rl *keepx,
+                       const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch,
+                       const int *ctl, const TW<Rl> *twy, int *groups_out, cudaStream_t s);
+
+}  // namespace pss

@@ -21,6 +21,9 @@
 #pragma once
 #include "fft_core.cuh"
 
+#include <type_traits>
+#include <utility>
+
 namespace pss {
 
 // ----------------------------------------------------------------------------
@@ -233,6 +236,17 @@ __global__ void __launch_bounds__(RowCfgOf<Rl, N, Op>::THREADS, RowCfgOf<Rl, N, 
     cp_async_wait<0>();
 }
 
+// input k of a column op: op.in(k, field) where the op chooses its source
+// buffer per field, else op.in(k)
+template <class Op, class = void> struct FieldIn : std::false_type {};
+template <class Op>
+struct FieldIn<Op, std::void_t<decltype(std::declval<const Op &>().in(0, int64_t(0)))>> : std::true_type {};
+template <class Op> __device__ __forceinline__ auto col_in(const Op &op, int k, int64_t field)
+{
+    if constexpr (FieldIn<Op>::value) return op.in(k, field);
+    else return op.in(k);
+}
+
 // tiles: (NX / W) column groups per field, fields in order
 template <class Rl, int N, class Op>
 __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op>::THREADS, ColCfgOf<Rl, N, Op>::MIN_CTAS)
@@ -253,7 +267,7 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op>::THREADS, ColCfgOf<Rl, N, 
             const int64_t field = tile / groups, x = (tile % groups) * C::W + c;
 #pragma unroll
             for (int k = 0; k < NIN; ++k)
-                stage_line<C::P, C::T>(line(b, k), op.in(k) + field * N * nx + x, nx, t);
+                stage_line<C::P, C::T>(line(b, k), col_in(op, k, field) + field * N * nx + x, nx, t);
         }
         cp_async_commit();
     };

@@ -169,3 +169,73 @@ def test_graph_and_direct_launches_agree_bitwise(lib, cuda_device, eq, monkeypat
     for a, b in zip(out[0][0], out[1][0]):
         assert np.array_equal(a, b)
     assert out[0][1] == out[1][1]
+
+
+# ---------------------------------------------------------------------------
+# Implicit-midpoint variant: the Jacobian of (w^k + w^n)/2 in place of the
+# trapezoidal (J^k + J^n)/2, same Crank-Nicolson diffusion
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [64, 128])
+def test_midpoint_matches_oracle(lib, orc, cuda_device, precision, n):
+    L, nu, dt, steps = 2 * math.pi, 1e-3, 2.5e-3, 20
+    w0 = S.ns_power_law(n)
+    ref, iters, ok = orc.ns_run(orc.ns_init(w0, True), L, L, nu, dt, steps, scheme="midpoint")
+    assert ok
+    g = lib.Grid("ns", n, precision, lx=L, ly=L, dt=dt, nu=nu, tol=1e-10, dealias=1, scheme="midpoint")
+    g.set_state(w0[None])
+    g.step(steps)
+    err = rel_l2(g.get_state()[0], orc.ns_field(ref))
+    assert err <= (TOL64 if precision == "fp64" else 1e-5), err
+    if precision == "fp64":
+        assert g.stats()[1] == int(iters.sum())
+
+
+def test_midpoint_taylor_green_equals_cn_closed_form(lib, cuda_device):
+    # J = 0: both schemes are the Crank-Nicolson amplification of Table 4's run
+    g0 = _golden("ns_taylor_green_table4.txt")
+    n, steps, dt, nu = 64, int(g0["steps"]), g0["dt"], g0["nu"]
+    g = lib.Grid("ns", n, "fp64", lx=1.0, ly=1.0, dt=dt, nu=nu, tol=g0["tol"], dealias=0, scheme="midpoint")
+    g.set_state(S.taylor_green_paper(n)[None])
+    g.step(steps)
+    err = np.abs(g.get_state()[0] - S.taylor_green_paper(n, t=steps * dt, nu=nu)).max()
+    assert abs(err - _cn_error(4 * math.pi, 8 * math.pi ** 2, nu, dt, steps)) <= 1e-10
+
+
+def test_midpoint_inviscid_keeps_energy_and_enstrophy(lib, cuda_device):
+    # nu = 0 with the 2/3 rule: the midpoint rule conserves every quadratic
+    # invariant of the truncated system, up to the fixed-point tolerance
+    n, L, dt, steps = 64, 2 * math.pi, 1e-2, 20
+    out = {}
+    for scheme in ("midpoint", "cn"):
+        g = lib.Grid("ns", n, "fp64", lx=L, ly=L, dt=dt, nu=0.0, tol=1e-24, max_iter=200, dealias=1,
+                     scheme=scheme)
+        g.set_state(S.ns_power_law(n)[None])
+        (c0, z0, e0), = g.conserved()
+        g.step(steps)
+        (c1, z1, e1), = g.conserved()
+        out[scheme] = (abs(z1 - z0) / z0, abs(e1 - e0) / e0)
+    assert max(out["midpoint"]) <= 1e-11
+    assert out["cn"][0] > 1e-9  # the trapezoidal rule does not conserve them
+
+
+def test_midpoint_graph_direct_and_resume_agree_bitwise(lib, cuda_device, monkeypatch):
+    n, L = 64, 2 * math.pi
+    kw = dict(lx=L, ly=L, dt=2.5e-3, nu=1e-3, scheme="midpoint")
+    w0 = S.ns_power_law(n, batch=2)
+    out = []
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("PSS_GRAPHS", graphs)
+        g = lib.Grid("ns", n, "fp32", batch=2, **kw)
+        g.set_state(w0)
+        g.step(4)
+        ck = g.checkpoint()
+        g.step(5)
+        out.append((g.get_state(), g.stats()))
+        h = lib.Grid("ns", n, "fp32", batch=2, **kw)
+        h.restore(ck)
+        h.step(5)
+        assert np.array_equal(h.get_state(), out[-1][0]) and h.stats() == out[-1][1]
+        g.close()
+        h.close()
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
