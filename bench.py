@@ -36,6 +36,7 @@ UNIT = "Gpt-steps/s"
 N = 1024
 L = 20 * math.pi
 DT = 1e-3
+FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate (no measured FP64 peak is available)
 E2E_STEPS = 2000  # one full solve of the 1024^2 configuration per e2e iteration
 
 
@@ -51,6 +52,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-other", action="store_true", help="skip the SG / NS / 4096^2 NLS lines")
+    ap.add_argument("--paper-tables", action="store_true",
+                    help="replay the runs of Tables 2-4 instead (one JSON line with both timings)")
     ap.add_argument("--serve-requests", type=int, default=120)
     return ap.parse_args()
 
@@ -227,6 +231,128 @@ def run_reference(args):
     return 0
 
 
+def timed_steps(grid, steps: int, stream) -> float:
+    """Milliseconds per step of `steps` steps, CUDA events on the grid's stream."""
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    grid.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    grid.sync()  # reports a Navier-Stokes non-convergence, if any
+    return e0.elapsed_time(e1) / steps
+
+
+def other_paths(stream, rank: int):
+    """Device-timed throughput of the other equations at their workload grids
+    (sine-Gordon 2048^2, Navier-Stokes 4096^2 both schemes) and of the NLS step
+    at 4096^2, where one pass moves 256 MiB per field pair."""
+    import paper_1206_3215_gb300 as P
+    import synthetic as S
+    out = {}
+    sc = stream.cuda_stream
+
+    def rate(points, ms):
+        return points / (ms / 1e3) / 1e9
+
+    # sine-Gordon, Eq. 3: 2048^2, box [-5 pi, 5 pi)^2, dt 1e-3
+    for prec, B, K in (("fp32", 8, 50), ("fp64", 4, 5)):
+        n, Ls = 2048, 10 * math.pi
+        u0, v0 = S.sg_gaussian(n, batch=B, seed=S.SEED_BASE + 2 + 100000 * rank)
+        g = P.Grid("sg", n, prec, batch=B, lx=Ls, ly=Ls, dt=1e-3, stream=sc)
+        g.set_state(u0, v0)
+        g.step(3)
+        ms = timed_steps(g, K, stream)
+        out[f"sg_2048_{prec}"] = {"value": rate(B * n * n, ms), "unit": UNIT, "batch": B, "steps": K,
+                                  "ms_per_step": ms}
+        g.close()
+    # Navier-Stokes 4096^2, [0, 2 pi)^2, nu 1e-3, dt 2.5e-4, tol 1e-10, 2/3 rule
+    for scheme in ("cn", "midpoint"):
+        n, Ln = 4096, 2 * math.pi
+        g = P.Grid("ns", n, "fp32", lx=Ln, ly=Ln, dt=2.5e-4, nu=1e-3, tol=1e-10, dealias=1, scheme=scheme,
+                   stream=sc)
+        g.set_state(S.ns_power_law(n, seed=S.SEED_BASE + 3 + 100000 * rank)[None])
+        g.step(2)
+        g.sync()
+        u0 = g.stats()[1]
+        K = 10
+        ms = timed_steps(g, K, stream)
+        out[f"ns_4096_fp32_{scheme}"] = {"value": rate(n * n, ms), "unit": UNIT, "steps": K, "ms_per_step": ms,
+                                         "jacobians_per_step": (g.stats()[1] - u0) / K}
+        g.close()
+    # NLS at 4096^2 (2 fields, 256 MiB of state): the row/column pass roofline
+    n, B, K = 4096, 2, 50
+    f = S.nls_gaussian(n, seed=S.SEED_BASE + 1 + 100000 * rank, batch=B).astype("complex64")
+    g = P.Grid("nls", n, "fp32", batch=B, lx=L, ly=L, dt=DT, stream=sc)
+    g.set_state(f)
+    g.step(3)
+    P.pss_set_profiling(g.h, True)
+    ms = timed_steps(g, K, stream)
+    prof = P.pss_profile_read(g.h)
+    P.pss_set_profiling(g.h, False)
+    hbm, _ = peaks()
+    pass_bytes = 2 * B * n * n * 8
+    row_ms = prof["row"][1] / max(prof["row"][0], 1)
+    col_ms = prof["col"][1] / max(prof["col"][0], 1)
+    out["nls_4096_fp32"] = {"value": rate(B * n * n, ms), "unit": UNIT, "batch": B, "steps": K,
+                            "ms_per_step": ms, "row_frac": pass_bytes / (row_ms / 1e3) / 1e9 / hbm,
+                            "col_frac": pass_bytes / (col_ms / 1e3) / 1e9 / hbm,
+                            "step_frac": 2 * pass_bytes / (ms / 1e3) / 1e9 / hbm}
+    g.close()
+    return out
+
+
+# Best GPU time in seconds per grid size printed in Tables 2-4 (NVIDIA Fermi
+# M2070, FP64, cuFFT 4.1; the fastest of the CUDA Fortran, CUDA C and OpenACC
+# columns).  Table 2: NLS, box [-5 pi, 5 pi)^2, dt 1e-5, 20 steps.  Table 3:
+# sine-Gordon, box [-5 pi, 5 pi)^2, dt 1e-3, 500 steps.  Table 4: Navier-Stokes
+# Taylor-Green on [0, 1)^2, dt 1.25e-3, 20 steps, tol 1e-10.
+PAPER_BEST_GPU_S = {
+    "nls": {64: 0.00272, 128: 0.00366, 256: 0.00802, 512: 0.0234, 1024: 0.0851, 2048: 0.334, 4096: 1.49,
+            8192: 6.30},
+    "sg": {64: 0.025, 128: 0.031, 256: 0.065, 512: 0.260, 1024: 0.976, 2048: 4.007, 4096: 16.53, 8192: 85.45},
+    "ns": {64: 0.0151, 128: 0.0201, 256: 0.0418, 512: 0.119, 1024: 0.357, 2048: 1.386, 4096: 5.814},
+}
+PAPER_RUNS = {"nls": (20, 1e-5), "sg": (500, 1e-3), "ns": (20, 1.25e-3)}
+
+
+def run_paper_tables(args):
+    """Time the runs of Tables 2-4 as the paper did (the time-stepping loop
+    only, state resident, after set-up) in FP64 and FP32, one field each."""
+    import torch
+
+    import paper_1206_3215_gb300 as P
+    import synthetic as S
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    rows = []
+    for eq, table in PAPER_BEST_GPU_S.items():
+        steps, dt = PAPER_RUNS[eq]
+        for n, paper_s in table.items():
+            for prec in ("fp64", "fp32"):
+                if eq == "nls":
+                    kw = dict(lx=10 * math.pi, ly=10 * math.pi, dt=dt)
+                    state = (S.nls_gaussian(n, x0=-5 * math.pi, L=10 * math.pi),)
+                elif eq == "sg":
+                    kw = dict(lx=10 * math.pi, ly=10 * math.pi, dt=dt)
+                    state = S.sg_gaussian(n)
+                else:
+                    kw = dict(lx=1.0, ly=1.0, dt=dt, nu=0.1, tol=1e-10, dealias=0)
+                    state = (S.taylor_green_paper(n),)
+                g = P.Grid(eq, n, prec, stream=stream.cuda_stream, **kw)
+                g.set_state(*(a[None] for a in state))
+                g.step(steps)  # the first call of a step count captures its graph
+                g.set_state(*(a[None] for a in state))
+                ms = timed_steps(g, steps, stream) * steps
+                rows.append({"eq": eq, "n": n, "precision": prec, "steps": steps, "seconds": ms / 1e3,
+                             "paper_best_gpu_s": paper_s, "speedup_vs_paper": paper_s / (ms / 1e3)})
+                g.close()
+    print(json.dumps({"paper_tables": rows, "note": "paper: Fermi M2070, FP64; here: one GB300, one field"}),
+          flush=True)
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -318,8 +444,17 @@ def run_ours(args):
         f1.record(stream)
         torch.cuda.synchronize(dev)
         ms64 = f0.elapsed_time(f1)
-        fp64 = {"value": world * B * n * n * k64 / (ms64 / 1e3) / 1e9, "unit": UNIT, "steps": k64,
-                "ms_per_step": ms64 / k64}
+        v64 = world * B * n * n * k64 / (ms64 / 1e3) / 1e9
+        # FP64 on GB300 is bound by the FP64 units, not HBM: flops by the
+        # 5 N log2 N convention for the forward + inverse 2D transform of a
+        # step (pointwise work not counted), against the nominal FP64 rate
+        flops_pt = 2 * 5 * 2 * math.log2(n)
+        achieved64 = v64 / world * flops_pt  # GFLOP/s per GPU
+        fp64 = {"value": v64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
+                "roofline": {"bound": "alu", "achieved": achieved64, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                             "frac": achieved64 / FP64_PEAK_GFLOPS, "peak_kind": "nominal",
+                             "flops_per_point_step": flops_pt,
+                             "convention": "5 N log2 N per complex transform, 2D forward + inverse per step"}}
         g64.close()
 
     # end to end through the public API with host buffers: one full solve of
@@ -368,6 +503,8 @@ def run_ours(args):
                  "wall_s": st["wall_s"], "pools": st["pools"], "rounds": st["rounds"],
                  "mix": "NLS/SG/NS FP32, N in {128,256,512,1024,2048}, 50-500 steps, 8 slots per pool"}
 
+    other = None if args.no_other else other_paths(stream, rank)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         try:
@@ -391,6 +528,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "serving": serve,
+            "other_paths": other,
             "gpu_launches": prof["launches"],
             "clocks": clk.summary(),
         }
@@ -404,6 +542,8 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.paper_tables:
+        return run_paper_tables(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
