@@ -11,25 +11,34 @@
 
 namespace pss {
 
-__device__ __forceinline__ void sincos_(float a, float *s, float *c) { sincosf(a, s, c); }
-__device__ __forceinline__ void sincos_(double a, double *s, double *c) { sincos(a, s, c); }
-
 // sin(th) and cos(th) - 1 of the nonlinear phase, both without cancellation.
-// For |th| <= 1/2 (always, at the workload's dt |psi|^2 ~ 1e-3) their Taylor
-// series: the first omitted terms are th^11/11! and th^12/12!, below 3e-11
-// relative to the kept sums.  Otherwise sin and cos of th/2 from the math
-// library: sin th = 2 s c, cos th - 1 = -2 s^2.
+// Taylor series on |a| <= A (FP32: 1/2, FP64: 1/16), where the first omitted
+// terms (a^11/11!, a^12/12!) are below 3e-11 (FP32) and 2e-20 (FP64)
+// relative to the kept sums.  At the workload's dt |psi|^2 ~ 1e-3 that is the
+// whole computation.  A larger phase is first halved k times (exact scaling
+// by 2^-k) and then doubled back with
+//   sin 2a = 2 sin a (1 + (cos a - 1)),  cos 2a - 1 = 2 (cos a - 1)(cos a - 1 + 2),
+// which keeps both terms free of cancellation; k is bounded by the exponent
+// range, so a non-finite phase ends in NaN after a bounded loop.
 template <class Rl> __device__ __forceinline__ void phase_terms(Rl th, Rl &sn, Rl &cm1)
 {
-    if (fabs(th) <= Rl(0.5)) {
-        const Rl t2 = th * th;
-        sn = th * (Rl(1) + t2 * (Rl(-1.0 / 6) + t2 * (Rl(1.0 / 120) + t2 * (Rl(-1.0 / 5040) + t2 * Rl(1.0 / 362880)))));
-        cm1 = t2 * (Rl(-0.5) + t2 * (Rl(1.0 / 24) + t2 * (Rl(-1.0 / 720) + t2 * (Rl(1.0 / 40320) + t2 * Rl(-1.0 / 3628800)))));
-    } else {
-        Rl sh, ch;
-        sincos_(Rl(0.5) * th, &sh, &ch);
-        sn = Rl(2) * sh * ch;
-        cm1 = Rl(-2) * sh * sh;
+    constexpr int KMAX = sizeof(Rl) == 4 ? 130 : 1026;
+    constexpr Rl A = sizeof(Rl) == 4 ? Rl(0.5) : Rl(0.0625);
+    Rl a = th;
+    int k = 0;
+#pragma unroll 1
+    while (!(fabs(a) <= A) && k < KMAX) {
+        a *= Rl(0.5);
+        ++k;
+    }
+    const Rl t2 = a * a;
+    sn = a * (Rl(1) + t2 * (Rl(-1.0 / 6) + t2 * (Rl(1.0 / 120) + t2 * (Rl(-1.0 / 5040) + t2 * Rl(1.0 / 362880)))));
+    cm1 = t2 * (Rl(-0.5) + t2 * (Rl(1.0 / 24) + t2 * (Rl(-1.0 / 720) + t2 * (Rl(1.0 / 40320) + t2 * Rl(-1.0 / 3628800)))));
+#pragma unroll 1
+    for (; k > 0; --k) {
+        const Rl s2 = Rl(2) * sn * (Rl(1) + cm1);
+        cm1 = Rl(2) * cm1 * (cm1 + Rl(2));
+        sn = s2;
     }
 }
 

@@ -37,6 +37,15 @@ namespace pss {
 #ifndef PSS_COL_P
 #define PSS_COL_P 32
 #endif
+#ifndef PSS_BIG_N
+#define PSS_BIG_N 2048
+#endif
+#ifndef PSS_ROW_P_BIG
+#define PSS_ROW_P_BIG PSS_ROW_P
+#endif
+#ifndef PSS_COL_P_BIG
+#define PSS_COL_P_BIG PSS_COL_P
+#endif
 #ifndef PSS_ROW_P64
 #define PSS_ROW_P64 16
 #endif
@@ -48,6 +57,9 @@ namespace pss {
 #endif
 #ifndef PSS_COL_THREADS
 #define PSS_COL_THREADS 256
+#endif
+#ifndef PSS_COL_WIDE_THREADS
+#define PSS_COL_WIDE_THREADS 256
 #endif
 // FP32 (measured, 1024^2): one shared-memory buffer per CTA and two CTAs per
 // SM (<= 128 registers) beat a double-buffered CTA alone by 9 %; FP64 keeps
@@ -71,14 +83,20 @@ template <class Rl> struct Shape {
     // points per thread of the row and column transforms
     static constexpr int RP = sizeof(Rl) == 4 ? PSS_ROW_P : PSS_ROW_P64;
     static constexpr int CP = sizeof(Rl) == 4 ? PSS_COL_P : PSS_COL_P64;
-    __host__ __device__ static constexpr int rowP(int n) { return n < RP ? n : RP; }
-    __host__ __device__ static constexpr int colP(int n) { return n < CP ? n : CP; }
+    // rows of at least PSS_BIG_N points may use PSS_ROW_P_BIG / PSS_COL_P_BIG
+    static constexpr int RPB = sizeof(Rl) == 4 ? PSS_ROW_P_BIG : RP;
+    static constexpr int CPB = sizeof(Rl) == 4 ? PSS_COL_P_BIG : CP;
+    __host__ __device__ static constexpr int rowP(int n) { return n < RP ? n : n >= PSS_BIG_N ? RPB : RP; }
+    __host__ __device__ static constexpr int colP(int n) { return n < CP ? n : n >= PSS_BIG_N ? CPB : CP; }
     // columns per tile: 64-byte row segments (FP32) when the thread budget
-    // and shared memory (two buffers) allow
-    __host__ __device__ static constexpr int cols(int n, int p)
+    // and shared memory (nbuf buffers) allow; with `wide`, a tile of two or
+    // more columns may use up to PSS_COL_WIDE_THREADS threads
+    __host__ __device__ static constexpr int cols(int n, int p, int nbuf = 2, bool wide = false)
     {
         int w = sizeof(Rl) == 4 ? 8 : 4;
-        while (w > 1 && ((long)2 * w * (n + n / 16) * ESZ > 200 * 1024L || w * (n / p) > PSS_COL_THREADS)) w /= 2;
+        while (w > 1 && ((long)nbuf * w * (n + n / 16) * ESZ > 200 * 1024L ||
+                         w * (n / p) > (wide ? PSS_COL_WIDE_THREADS : PSS_COL_THREADS)))
+            w /= 2;
         return w;
     }
 };
@@ -128,13 +146,16 @@ template <class Rl, int N, int NIN, bool LEAN = false, int PMAX = 32> struct Row
     static constexpr int MAXB = LEAN ? Shape<Rl>::MAX_NBUF : 2;
     static constexpr int NBUF = (MAXB > 1 && size_t(2) * BUF * Shape<Rl>::ESZ <= SMEM_LIMIT) ? 2 : 1;
     static constexpr size_t SMEM = size_t(NBUF) * BUF * Shape<Rl>::ESZ;
-    static constexpr int MIN_CTAS = LEAN ? Shape<Rl>::MIN_CTAS : 1;
+    // resident CTAs the registers are budgeted for: at most 512 threads per SM
+    // at 128 registers each
+    static constexpr int MIN_CTAS = LEAN ? (THREADS * Shape<Rl>::MIN_CTAS <= 512 ? Shape<Rl>::MIN_CTAS : 1) : 1;
 };
 
 template <class Rl, int N, int NIN, bool LEAN = false, int PMAX = 32> struct ColCfg {
     static constexpr int P = Shape<Rl>::colP(N) < PMAX ? Shape<Rl>::colP(N) : PMAX;
     static constexpr int T = N / P;
-    static constexpr int W = Shape<Rl>::cols(N, P);
+    // lean ops (one buffer, <= 128 registers) may take the wide tiles
+    static constexpr int W = LEAN ? Shape<Rl>::cols(N, P, NIN * Shape<Rl>::MAX_NBUF, true) : Shape<Rl>::cols(N, P);
     static constexpr int PADLOG = pad_log(P);
     static constexpr int STRIDE = col_stride(N + (N >> PADLOG), W, Shape<Rl>::ESZ);
     static constexpr int THREADS = W * T;
@@ -143,7 +164,9 @@ template <class Rl, int N, int NIN, bool LEAN = false, int PMAX = 32> struct Col
     static constexpr int MAXB = LEAN ? Shape<Rl>::MAX_NBUF : 2;
     static constexpr int NBUF = (MAXB > 1 && size_t(2) * BUF * Shape<Rl>::ESZ <= SMEM_LIMIT) ? 2 : 1;
     static constexpr size_t SMEM = size_t(NBUF) * BUF * Shape<Rl>::ESZ;
-    static constexpr int MIN_CTAS = LEAN ? Shape<Rl>::MIN_CTAS : 1;
+    // resident CTAs the registers are budgeted for: at most 512 threads per SM
+    // at 128 registers each
+    static constexpr int MIN_CTAS = LEAN ? (THREADS * Shape<Rl>::MIN_CTAS <= 512 ? Shape<Rl>::MIN_CTAS : 1) : 1;
 };
 
 template <class Rl, int N, class Op> using RowCfgOf = RowCfg<Rl, N, Op::NIN, Op::LEAN, Op::PMAX>;

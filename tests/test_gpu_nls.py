@@ -36,6 +36,27 @@ def test_config1_64_matches_oracle(lib, orc, cuda_device, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("phase", [0.4, 2.7, 41.3, -3.3])
+def test_large_nonlinear_phase_plane_wave(lib, cuda_device, precision, phase):
+    # sigma |psi|^2 dt beyond the Taylor range of the phase (|th| > 1/2): the
+    # halving and doubling path.  The plane wave keeps |psi| = A, so every
+    # step is exact: psi(t) = psi0 exp(-i (|k|^2 + sigma A^2) t)
+    n, dt, steps = 64, 1e-3, 20
+    sigma = math.copysign(1.0, phase)
+    A = math.sqrt(abs(phase) / dt)
+    p0 = S.nls_plane_wave(n, A=A, m=(3, 2))
+    g = _grid(lib, n, precision, dt=dt, sigma=sigma)
+    g.set_state(p0[None])
+    g.step(steps)
+    k2 = (2 * math.pi / L) ** 2 * 13
+    exact = p0 * np.exp(-1j * (k2 + sigma * A * A) * dt * steps)
+    err = rel_l2(g.get_state()[0], exact)
+    # the phase itself is rounded once per step: 20 |th| eps relative
+    eps = 2.2e-16 if precision == "fp64" else 1.2e-7
+    assert err <= 64 * steps * max(abs(phase), 1) * eps, err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_plane_wave_1024_closed_form(lib, cuda_device, precision):
     n, dt, steps, A = 1024, 1e-3, 2000, 0.5
     p0 = S.nls_plane_wave(n, A=A, m=(3, 2))

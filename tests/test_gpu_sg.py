@@ -40,6 +40,26 @@ def test_gaussian_matches_oracle(lib, orc, cuda_device, precision, n, steps):
     assert rel_l2(a[0] - b[0], ref_n - ref_m) <= (1e-8 if precision == "fp64" else 2e-3)
 
 
+@pytest.mark.parametrize("shift", [100.0, -2.0e4])
+def test_large_field_values_match_oracle(lib, orc, cuda_device, shift):
+    # u far from 0 exercises the FP32 argument reduction of sin u: a constant
+    # shift of u0 by `shift` (the Gaussian bump stays) against the FP64 oracle.
+    # Tolerance: the rounding of u itself (|u| eps32 relative to the O(1) bump)
+    # grows with |shift|
+    n, dt, steps = 64, 1e-3, 100
+    u0, v0 = S.sg_gaussian(n)
+    u0 = u0 + shift
+    un, um = orc.sg_init(u0, v0, L, L, dt)
+    un, um = orc.sg_run(un, um, L, L, dt, steps)
+    ref_n, _ = orc.sg_fields(un, um)
+    g = _grid(lib, n, "fp32", dt=dt)
+    g.set_state(u0[None], v0[None])
+    g.step(steps)
+    got = g.get_state()[0][0]
+    err = np.abs(got - ref_n).max()
+    assert err <= 8 * abs(shift) * 1.2e-7 + 2e-5, err
+
+
 def test_uniform_field_is_the_pendulum(lib, cuda_device):
     n, dt, steps, u0, v0 = 16, 1e-2, 300, 0.9, 0.3
     g = _grid(lib, n, "fp64", dt=dt)
