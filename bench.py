@@ -256,16 +256,17 @@ def other_paths(stream, rank: int):
     def rate(points, ms):
         return points / (ms / 1e3) / 1e9
 
-    # sine-Gordon, Eq. 3: 2048^2, box [-5 pi, 5 pi)^2, dt 1e-3
-    for prec, B, K in (("fp32", 8, 50), ("fp64", 4, 5)):
+    # sine-Gordon, Eq. 3: 2048^2, box [-5 pi, 5 pi)^2, dt 1e-3; full complex
+    # spectra and half spectra (real-to-complex rows)
+    for prec, B, K, rfft in (("fp32", 8, 50, 0), ("fp32", 8, 50, 1), ("fp64", 4, 5, 0), ("fp64", 4, 5, 1)):
         n, Ls = 2048, 10 * math.pi
         u0, v0 = S.sg_gaussian(n, batch=B, seed=S.SEED_BASE + 2 + 100000 * rank)
-        g = P.Grid("sg", n, prec, batch=B, lx=Ls, ly=Ls, dt=1e-3, stream=sc)
+        g = P.Grid("sg", n, prec, batch=B, lx=Ls, ly=Ls, dt=1e-3, stream=sc, rfft=rfft)
         g.set_state(u0, v0)
         g.step(3)
         ms = timed_steps(g, K, stream)
-        out[f"sg_2048_{prec}"] = {"value": rate(B * n * n, ms), "unit": UNIT, "batch": B, "steps": K,
-                                  "ms_per_step": ms}
+        out[f"sg_2048_{prec}" + ("_half" if rfft else "")] = {"value": rate(B * n * n, ms), "unit": UNIT,
+                                                              "batch": B, "steps": K, "ms_per_step": ms}
         g.close()
     # Navier-Stokes 4096^2, [0, 2 pi)^2, nu 1e-3, dt 2.5e-4, tol 1e-10, 2/3 rule
     for scheme in ("cn", "midpoint"):

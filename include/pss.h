@@ -92,14 +92,16 @@ typedef struct pss_params {
     int32_t dealias;   /* NS: 1 = 2/3-rule square truncation (3|m| < n) on J and w0   */
     void *stream;      /* cudaStream_t to enqueue on, or NULL for a library stream    */
     int32_t scheme;    /* NS: PSS_NS_CN or PSS_NS_MIDPOINT                             */
-    int32_t reserved;  /* must be 0                                                    */
+    int32_t rfft;      /* SG: 1 = step on half spectra (real-to-complex transforms,
+                          kx = 0 .. nx/2; Section 5.2's programs do the same);
+                          0 = full complex spectra.  Must be 0 for NLS and NS.     */
 } pss_params;
 
 typedef struct pss_grid pss_grid;
 
 /* Fill *p with defaults: NLS, FP32, 64x64, batch 1, box [-10pi,10pi)^2,
  * dt 1e-3, sigma +1, nu 1/10, tol 1e-10, max_iter 100, dealias 1,
- * scheme PSS_NS_CN. */
+ * scheme PSS_NS_CN, rfft 0. */
 void pss_default_params(pss_params *p);
 
 /* Create a grid: validates *p, allocates every device buffer the equation

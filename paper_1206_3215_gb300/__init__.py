@@ -41,7 +41,7 @@ class PssParams(ctypes.Structure):
         ("lx", ctypes.c_double), ("ly", ctypes.c_double),
         ("dt", ctypes.c_double), ("sigma", ctypes.c_double), ("nu", ctypes.c_double),
         ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("dealias", ctypes.c_int32),
-        ("stream", ctypes.c_void_p), ("scheme", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("stream", ctypes.c_void_p), ("scheme", ctypes.c_int32), ("rfft", ctypes.c_int32),
     ]
 
 

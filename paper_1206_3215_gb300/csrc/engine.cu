@@ -116,6 +116,20 @@ int pss_grid::init()
             (rc = upload_real<double>(this, kpx, &keepx)) || (rc = upload_real<double>(this, kpy, &keepy)))
             return rc;
     }
+    if (p.eq == PSS_EQ_SG && p.rfft) {
+        half = true;
+        sx = nx / 2 + 8;  // a multiple of every column-tile width
+        const size_t hb = size_t(sx) * size_t(ny) * size_t(batch) * esz;
+        for (int i = 0; i < 3; ++i) {
+            if ((rc = alloc(&hbuf[i], hb))) return rc;
+            if ((rc = cuda(cudaMemset(hbuf[i], 0, hb), "memset"))) return rc;
+        }
+        if ((rc = upload_twiddles(this, nx / 2, &twm))) return rc;
+        std::vector<double> kh(sx, 0.0);
+        for (int64_t m = 0; m <= nx / 2; ++m) kh[m] = kx2v[m];
+        if ((rc = p.precision == PSS_FP32 ? upload_real<float>(this, kh, &kx2h) : upload_real<double>(this, kh, &kx2h)))
+            return rc;
+    }
     if (p.eq == PSS_EQ_NLS) {
         // exp(-i k^2 tau) - 1 = (-2 sin^2(k^2 tau / 2), -sin(k^2 tau)) per axis,
         // tau = dt/2 (index 0) and dt (index 1); no cancellation for small k
@@ -395,6 +409,28 @@ template <class Rl> int sg_make_h(pss_grid *g)
     return g->cuda(fft_cols<Rl>(B<Rl>(g, 2), g->nx, g->ny, g->batch, +1, s, Tw<Rl>(g->twy), g->stream), "H");
 }
 
+// half spectra <-> full spectra of the sine-Gordon state
+template <class Rl> int sg_half_sync(pss_grid *g, bool to_half)
+{
+    int rc;
+    V2<Rl> *hu = static_cast<V2<Rl> *>(g->hbuf[0]), *hd = static_cast<V2<Rl> *>(g->hbuf[1]),
+           *hh = static_cast<V2<Rl> *>(g->hbuf[2]);
+    if (to_half) {
+        const size_t hb = size_t(g->sx) * size_t(g->ny) * size_t(g->batch) * g->esz;
+        const Rl s = Rl(1.0 / (double(g->nx) * double(g->ny)));
+        if ((rc = g->cuda(pack_half<Rl>(B<Rl>(g, 0), hu, g->nx, g->ny, g->sx, g->batch, g->stream), "pack")) ||
+            (rc = g->cuda(pack_half<Rl>(B<Rl>(g, 1), hd, g->nx, g->ny, g->sx, g->batch, g->stream), "pack")) ||
+            (rc = g->cuda(cudaMemcpyAsync(hh, hu, hb, cudaMemcpyDeviceToDevice, g->stream), "copy")) ||
+            (rc = g->cuda(fft_cols<Rl>(hh, g->sx, g->ny, g->batch, +1, s, Tw<Rl>(g->twy), g->stream), "H")))
+            return rc;
+        return PSS_OK;
+    }
+    if ((rc = g->cuda(unpack_half<Rl>(hu, B<Rl>(g, 0), g->nx, g->ny, g->sx, g->batch, g->stream), "unpack")) ||
+        (rc = g->cuda(unpack_half<Rl>(hd, B<Rl>(g, 1), g->nx, g->ny, g->sx, g->batch, g->stream), "unpack")))
+        return rc;
+    return PSS_OK;
+}
+
 template <class Rl> int sg_set(pss_grid *g, const void *u0, const void *v0, int where)
 {
     int rc;
@@ -419,6 +455,21 @@ template <class Rl> int sg_set(pss_grid *g, const void *u0, const void *v0, int 
 template <class Rl> int sg_step(pss_grid *g, int64_t n)
 {
     int rc;
+    if (g->half) {
+        V2<Rl> *u = static_cast<V2<Rl> *>(g->hbuf[0]), *d = static_cast<V2<Rl> *>(g->hbuf[1]),
+               *h = static_cast<V2<Rl> *>(g->hbuf[2]);
+        for (int64_t i = 0; i < n; ++i) {
+            if ((rc = g->pass_begin(0))) return rc;
+            cudaError_t e = sg_row_pass_r2c<Rl>(h, g->nx, g->sx, g->batch * g->ny, Tw<Rl>(g->twm), Tw<Rl>(g->twx),
+                                                g->stream);
+            if ((rc = g->pass_end()) || (rc = g->cuda(e, "sg row pass (half spectrum)"))) return rc;
+            if ((rc = g->pass_begin(1))) return rc;
+            e = sg_col_pass<Rl>(h, u, d, g->sx, g->ny, g->batch, Rt<Rl>(g->kx2h), Rt<Rl>(g->ky2), Rl(g->p.dt),
+                                Tw<Rl>(g->twy), g->stream, g->nx);
+            if ((rc = g->pass_end()) || (rc = g->cuda(e, "sg column pass (half spectrum)"))) return rc;
+        }
+        return PSS_OK;
+    }
     for (int64_t i = 0; i < n; ++i) {
         if ((rc = g->pass_begin(0))) return rc;
         cudaError_t e = sg_row_pass<Rl>(B<Rl>(g, 2), g->nx, g->batch * g->ny, Tw<Rl>(g->twx), g->stream);
@@ -797,14 +848,29 @@ int pss_grid::set_state(const void *a, const void *b, int where)
 #undef NLS
 #undef SG
 #undef NS
-    if (!rc) has_state = true;
+    if (!rc) {
+        has_state = true;
+        full_valid = true;
+        half_valid = false;
+    }
     return rc;
+}
+
+int pss_grid::half_sync(bool to_half)
+{
+    if (!half || (to_half ? half_valid : full_valid)) return PSS_OK;
+    int rc = p.precision == PSS_FP32 ? sg_half_sync<float>(this, to_half) : sg_half_sync<double>(this, to_half);
+    if (rc) return rc;
+    (to_half ? half_valid : full_valid) = true;
+    return PSS_OK;
 }
 
 int pss_grid::step_n(int64_t n)
 {
     if (n == 0) return PSS_OK;
     int rc;
+    if ((rc = half_sync(true))) return rc;
+    if (half) full_valid = false;
 #define NLS(R) nls_step<R>(this, n)
 #define SG(R) sg_step<R>(this, n)
 #define NS(R) ns_step<R>(this, n)
@@ -854,6 +920,8 @@ int pss_grid::step_n(int64_t n)
 
 int pss_grid::get_state(void *a, void *b, int where)
 {
+    int rc = half_sync(false);
+    if (rc) return rc;
 #define NLS(R) nls_get<R>(this, a, where)
 #define SG(R) sg_get<R>(this, a, b, where)
 #define NS(R) ns_get<R>(this, a, where)
@@ -865,18 +933,27 @@ int pss_grid::get_state(void *a, void *b, int where)
 
 int pss_grid::set_field(int64_t f, const void *a, const void *b, int where)
 {
-    int rc = p.precision == PSS_FP32 ? field_set<float>(this, f, a, b, where) : field_set<double>(this, f, a, b, where);
-    if (!rc) has_state = true;
+    int rc = half_sync(false);  // the other fields' full state must be current
+    if (rc) return rc;
+    rc = p.precision == PSS_FP32 ? field_set<float>(this, f, a, b, where) : field_set<double>(this, f, a, b, where);
+    if (!rc) {
+        has_state = true;
+        half_valid = false;
+    }
     return rc;
 }
 
 int pss_grid::get_field(int64_t f, void *a, void *b, int where)
 {
+    int rc = half_sync(false);
+    if (rc) return rc;
     return p.precision == PSS_FP32 ? field_get<float>(this, f, a, b, where) : field_get<double>(this, f, a, b, where);
 }
 
 int pss_grid::conserved(double *out)
 {
+    int rc = half_sync(false);
+    if (rc) return rc;
 #define NLS(R) nls_conserved<R>(this, out)
 #define SG(R) sg_conserved<R>(this, out)
 #define NS(R) ns_conserved<R>(this, out)
@@ -899,6 +976,7 @@ int pss_grid::checkpoint(void *buf_, int where, bool save)
     const int nstate = p.eq == PSS_EQ_SG ? 2 : 1;
     char *b = static_cast<char *>(buf_);
     int rc;
+    if (save && (rc = half_sync(false))) return rc;
     int src_of[2] = {0, 1};
     if (save && p.eq == PSS_EQ_NS) {
         rc = p.precision == PSS_FP32 ? ns_current<float>(this) : ns_current<double>(this);
@@ -938,6 +1016,8 @@ int pss_grid::checkpoint(void *buf_, int where, bool save)
         }
         if (rc || (rc = cuda(cudaStreamSynchronize(stream), "restore sync"))) return rc;
         has_state = true;
+        full_valid = true;
+        half_valid = false;
     }
     return PSS_OK;
 }

@@ -25,6 +25,17 @@ struct pss_grid {
     void *buf[8] = {};
     int nbuf = 0;
 
+    // sine-Gordon on half spectra (p.rfft): the stepping state lives in
+    // hbuf = {uhat, d, H}, [batch][ny][sx] with kx = 0 .. nx/2; the full
+    // buffers buf[0], buf[1] are rebuilt from it when a call reads the state
+    bool half = false;
+    int64_t sx = 0;
+    void *hbuf[3] = {};
+    void *twm = nullptr;   // twiddles of length nx/2
+    void *kx2h = nullptr;  // kx^2 of the half-spectrum columns (0 beyond nx/2)
+    bool half_valid = false, full_valid = true;
+    int half_sync(bool to_half);  // make the half (true) or full (false) copy current
+
     // tables (device)
     void *twx = nullptr, *twy = nullptr;                           // twiddles, precision
     void *ax[2] = {}, *by[2] = {};  // NLS exp(-i k^2 tau) per axis, [dt/2, dt]

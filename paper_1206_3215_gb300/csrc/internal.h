@@ -47,10 +47,24 @@ cudaError_t nls_col_pass(V2<Rl> *data, int64_t nx, int64_t ny, int64_t batch, Rl
 template <class Rl>
 cudaError_t sg_row_pass(V2<Rl> *h, int64_t nx, int64_t rows_total, const TW<Rl> *twx, cudaStream_t s);
 // Column pass: column FFT of S = F sin u^n; d <- d - (a u + dt^2 S)/(1 + a/4),
-// u <- u + d (a = dt^2 |k|^2), in place; H <- column inverse FFT of u / (nx ny).
+// u <- u + d (a = dt^2 |k|^2), in place; H <- column inverse FFT of u / (nreal ny).
+// nx is the row stride (columns processed), nreal the real row length (0: nx).
 template <class Rl>
 cudaError_t sg_col_pass(V2<Rl> *h, V2<Rl> *u, V2<Rl> *d, int64_t nx, int64_t ny, int64_t batch,
-                        const Rl *kx2, const Rl *ky2, Rl dt, const TW<Rl> *twy, cudaStream_t s);
+                        const Rl *kx2, const Rl *ky2, Rl dt, const TW<Rl> *twy, cudaStream_t s,
+                        int64_t nreal = 0);
+// Half-spectrum (real-to-complex) sine-Gordon row pass, k_sg_r2c.cu: rows of
+// stride sx holding kx = 0 .. nx/2; twm: twiddles of length nx/2, twn: of nx.
+template <class Rl>
+cudaError_t sg_row_pass_r2c(V2<Rl> *h, int64_t nx, int64_t sx, int64_t rows_total, const TW<Rl> *twm,
+                            const TW<Rl> *twn, cudaStream_t s);
+// full [batch][ny][nx] spectrum of real fields <-> half spectrum [batch][ny][sx]
+template <class Rl>
+cudaError_t pack_half(const V2<Rl> *full, V2<Rl> *half, int64_t nx, int64_t ny, int64_t sx, int64_t batch,
+                      cudaStream_t s);
+template <class Rl>
+cudaError_t unpack_half(const V2<Rl> *half, V2<Rl> *full, int64_t nx, int64_t ny, int64_t sx, int64_t batch,
+                        cudaStream_t s);
 
 // ---- Navier-Stokes passes (k_ns.cu) -------------------------------------------
 size_t ns_field_bytes();  // bytes of the per-field fixed-point record

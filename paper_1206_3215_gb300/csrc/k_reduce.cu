@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(RED_THREADS)
 {
     __shared__ double sh[3 * RED_THREADS];
     const int64_t f = blockIdx.y, n = nx * ny;
+    const int lgx = __ffsll(nx) - 1;  // nx is a power of two
     const V2<Rl> *p = psi + f * n, *h = hat + f * n;
     double a[3] = {0.0, 0.0, 0.0};
     for (int64_t i = int64_t(blockIdx.x) * RED_THREADS + threadIdx.x; i < n;
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(RED_THREADS)
         a[0] += m2;
         a[1] += m2 * m2;
         const V2<Rl> w = h[i];
-        a[2] += (kx2[i % nx] + ky2[i / nx]) * (double(w.x) * w.x + double(w.y) * w.y);
+        a[2] += (kx2[i & (nx - 1)] + ky2[i >> lgx]) * (double(w.x) * w.x + double(w.y) * w.y);
     }
     block_sum<3>(a, sh);
     if (threadIdx.x == 0)
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(RED_THREADS)
 {
     __shared__ double sh[3 * RED_THREADS];
     const int64_t f = blockIdx.y, n = nx * ny, o = f * n;
+    const int lgx = __ffsll(nx) - 1;  // nx is a power of two
     double a[3] = {0.0, 0.0, 0.0};
     for (int64_t i = int64_t(blockIdx.x) * RED_THREADS + threadIdx.x; i < n;
          i += int64_t(RED_BLOCKS) * RED_THREADS) {
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(RED_THREADS)
         a[1] += 2.0 * sh2 * sh2;
         const V2<Rl> u = U[o + i], d = D[o + i];
         const double br = double(u.x) - 0.5 * double(d.x), bi = double(u.y) - 0.5 * double(d.y);
-        a[2] += (kx2[i % nx] + ky2[i / nx]) * (br * br + bi * bi);
+        a[2] += (kx2[i & (nx - 1)] + ky2[i >> lgx]) * (br * br + bi * bi);
     }
     block_sum<3>(a, sh);
     if (threadIdx.x == 0)
@@ -123,6 +125,7 @@ __global__ void __launch_bounds__(RED_THREADS)
 {
     __shared__ double sh[3 * RED_THREADS];
     const int64_t f = blockIdx.y, n = nx * ny;
+    const int lgx = __ffsll(nx) - 1;  // nx is a power of two
     const int b = fs[f].idx;
     const V2<Rl> *w = (b == 0 ? w0 : b == 1 ? w1 : w2) + f * n;
     double a[3] = {0.0, 0.0, 0.0};
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(RED_THREADS)
          i += int64_t(RED_BLOCKS) * RED_THREADS) {
         const V2<Rl> z = w[i];
         const double m2 = double(z.x) * z.x + double(z.y) * z.y;
-        const double k2 = kx2[i % nx] + ky2[i / nx];
+        const double k2 = kx2[i & (nx - 1)] + ky2[i >> lgx];
         if (i == 0) a[0] += double(z.x);
         a[1] += m2;
         if (k2 > 0) a[2] += m2 / k2;
@@ -241,6 +244,7 @@ __global__ void __launch_bounds__(RED_THREADS)
 {
     __shared__ double sh[3 * RED_THREADS];
     const int64_t f = blockIdx.y, n = nx * ny;
+    const int lgx = __ffsll(nx) - 1;  // nx is a power of two
     const V2<Rl> *p = psi + f * n, *h = hat + f * n;
     double a[3] = {0.0, 0.0, 0.0};
     for (int64_t i = int64_t(blockIdx.x) * RED_THREADS + threadIdx.x; i < n;
@@ -250,7 +254,7 @@ __global__ void __launch_bounds__(RED_THREADS)
         a[0] += m2;
         a[1] += m2 * m2;
         const V2<Rl> w = h[i];
-        a[2] += (wavenumber2(i % nx, nx, dkx) + wavenumber2(i / nx, ny, dky)) *
+        a[2] += (wavenumber2(i & (nx - 1), nx, dkx) + wavenumber2(i >> lgx, ny, dky)) *
                 (double(w.x) * w.x + double(w.y) * w.y);
     }
     block_sum<3>(a, sh);

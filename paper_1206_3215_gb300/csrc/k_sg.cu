@@ -18,39 +18,11 @@
 // forward (F sin u^n), updates uhat and d in place, and writes the column
 // inverse transform of the new uhat as the next H.
 #include "launch.cuh"
+#include "sg_sin.cuh"
 
 namespace pss {
 
-// FP32 sin u: Cody-Waite reduction modulo pi/2 and Taylor polynomials on
-// [-pi/4, pi/4].  pi/2 = C1 + C2 + C3 (each a float, 72 bits together, from
-// the double-double pi/2 below), subtracted with fused multiply-adds, so the
-// reduced argument is accurate to a few ulp while |k| < 2^20 (|u| < 1.6e6).
-// The omitted Taylor terms r^11/11! and r^12/12! are below 2e-9 on the
-// interval.  A non-finite u gives NaN (no loop, no library slow path).
-namespace sinc {
-constexpr double HI = 1.5707963267948966, LO = 6.123233995736766e-17;  // pi/2 = HI + LO
-constexpr float C1 = float(HI);
-constexpr float C2 = float(HI - double(C1));
-constexpr float C3 = float((HI - double(C1) - double(C2)) + LO);
-}  // namespace sinc
-#ifndef PSS_SG_LIBM_SIN
-#define PSS_SG_LIBM_SIN 0
-#endif
-__device__ __forceinline__ float sin_(float x)
-{
-    if constexpr (PSS_SG_LIBM_SIN) return sinf(x);
-    const float k = rintf(x * float(2.0 / 3.14159265358979323846));
-    float r = __fmaf_rn(-k, sinc::C1, x);
-    r = __fmaf_rn(-k, sinc::C2, r);
-    r = __fmaf_rn(-k, sinc::C3, r);
-    const float r2 = r * r;
-    const float sn = __fmaf_rn(r * r2, -1.0f / 6 + r2 * (1.0f / 120 + r2 * (-1.0f / 5040 + r2 * (1.0f / 362880))), r);
-    const float cs = 1.0f + r2 * (-0.5f + r2 * (1.0f / 24 + r2 * (-1.0f / 720 + r2 * (1.0f / 40320 + r2 * (-1.0f / 3628800)))));
-    const int q = int(k) & 3;
-    const float v = (q & 1) ? cs : sn;
-    return (q & 2) ? -v : v;
-}
-__device__ __forceinline__ double sin_(double a) { return sin(a); }
+template <class Rl> __device__ __forceinline__ Rl sin_(Rl a) { return sg_sin(a); }
 // correctly rounded reciprocal
 __device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
 __device__ __forceinline__ double rcp_(double a) { return __drcp_rn(a); }
@@ -156,18 +128,20 @@ cudaError_t sg_row_pass(V2<Rl> *h, int64_t nx, int64_t rows_total, const TW<Rl> 
     return launch_row<Rl>(nx, SgRow<Rl>{h}, twx, rows_total, s);
 }
 
+// nx: row stride of the arrays (the columns processed); nreal: points per
+// row of the real-space field (nx for full spectra, more for half spectra)
 template <class Rl>
 cudaError_t sg_col_pass(V2<Rl> *h, V2<Rl> *u, V2<Rl> *d, int64_t nx, int64_t ny, int64_t batch,
-                        const Rl *kx2, const Rl *ky2, Rl dt, const TW<Rl> *twy, cudaStream_t s)
+                        const Rl *kx2, const Rl *ky2, Rl dt, const TW<Rl> *twy, cudaStream_t s, int64_t nreal)
 {
-    SgCol<Rl> op{h, u, d, kx2, ky2, dt * dt, Rl(1.0 / (double(nx) * double(ny))), nx};
+    SgCol<Rl> op{h, u, d, kx2, ky2, dt * dt, Rl(1.0 / (double(nreal > 0 ? nreal : nx) * double(ny))), nx};
     return launch_col<Rl>(ny, nx, op, twy, batch, s);
 }
 
 #define PSS_INST(Rl)                                                                              \
     template cudaError_t sg_row_pass<Rl>(V2<Rl> *, int64_t, int64_t, const TW<Rl> *, cudaStream_t); \
     template cudaError_t sg_col_pass<Rl>(V2<Rl> *, V2<Rl> *, V2<Rl> *, int64_t, int64_t, int64_t,   \
-                                         const Rl *, const Rl *, Rl, const TW<Rl> *, cudaStream_t);
+                                         const Rl *, const Rl *, Rl, const TW<Rl> *, cudaStream_t, int64_t);
 PSS_INST(float)
 PSS_INST(double)
 

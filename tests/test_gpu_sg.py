@@ -137,3 +137,92 @@ def test_config3_size_matches_oracle_over_100_steps(lib, orc, cuda_device):
     g32.step(steps)
     a32, _ = g32.get_state()
     assert rel_l2(a32[0], ref_n) <= TOL32
+
+
+# ---------------------------------------------------------------------------
+# Half spectra (rfft = 1): the same scheme stepped on kx = 0 .. nx/2 with
+# real-to-complex row transforms
+
+def _half(lib, n, precision, batch=1, dt=1e-3):
+    nx, ny = (n, n) if isinstance(n, int) else n
+    return lib.Grid("sg", (nx, ny), precision, batch=batch, lx=L, ly=L, x0=-L / 2, y0=-L / 2, dt=dt, rfft=1)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,steps", [(16, 50), (64, 200), (256, 100)])
+def test_half_spectrum_matches_oracle(lib, orc, cuda_device, precision, n, steps):
+    dt = 1e-3
+    u0, v0 = S.sg_gaussian(n)
+    un, um = orc.sg_init(u0, v0, L, L, dt)
+    un, um = orc.sg_run(un, um, L, L, dt, steps)
+    ref_n, ref_m = orc.sg_fields(un, um)
+    g = _half(lib, n, precision, dt=dt)
+    g.set_state(u0[None], v0[None])
+    g.step(steps)
+    a, b = g.get_state()
+    tol = TOL64 if precision == "fp64" else TOL32
+    assert rel_l2(a[0], ref_n) <= tol
+    assert rel_l2(b[0], ref_m) <= tol
+    assert rel_l2(a[0] - b[0], ref_n - ref_m) <= (1e-8 if precision == "fp64" else 2e-3)
+
+
+def test_half_spectrum_non_square_matches_oracle(lib, orc, cuda_device):
+    nx, ny, dt, steps = 128, 64, 1e-3, 60
+    x = S.grid_coords(nx, -L / 2, L)
+    y = S.grid_coords(ny, -L / 2, L)
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    u0 = 0.5 * np.exp(-(X ** 2 + 2 * Y ** 2) / 4) + 0.1 * np.cos(X)
+    v0 = 0.2 * np.sin(Y)
+    un, um = orc.sg_init(u0, v0, L, L, dt)
+    un, um = orc.sg_run(un, um, L, L, dt, steps)
+    ref_n, _ = orc.sg_fields(un, um)
+    g = _half(lib, (nx, ny), "fp64", dt=dt)
+    g.set_state(u0[None], v0[None])
+    g.step(steps)
+    assert rel_l2(g.get_state()[0][0], ref_n) <= TOL64
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_half_spectrum_hamiltonian_matches_full_path(lib, cuda_device, precision):
+    n, steps = 128, 300
+    u0, v0 = S.sg_gaussian(n)
+    out = []
+    for grid in (_grid(lib, n, precision), _half(lib, n, precision)):
+        grid.set_state(u0[None], v0[None])
+        grid.step(steps)
+        (h,), = grid.conserved()
+        out.append(h)
+    assert abs(out[0] - out[1]) / out[0] <= (1e-12 if precision == "fp64" else 2e-6)
+
+
+def test_half_spectrum_batch_fields_resume_and_graphs(lib, cuda_device, monkeypatch):
+    # fields of a batch equal their solo runs bit for bit; set/get of one
+    # field, checkpoint resume and graph vs direct launches are bitwise too
+    n = 64
+    u0, v0 = S.sg_gaussian(n, batch=3)
+    res = []
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("PSS_GRAPHS", graphs)
+        g = _half(lib, n, "fp32", batch=3)
+        g.set_state(u0, v0)
+        g.step(20)
+        ck = g.checkpoint()
+        g.step(20)
+        a, b = g.get_state()
+        for i in range(3):
+            h = _half(lib, n, "fp32")
+            h.set_state(u0[i:i + 1], v0[i:i + 1])
+            h.step(40)
+            a1, b1 = h.get_state()
+            assert np.array_equal(a1[0], a[i]) and np.array_equal(b1[0], b[i])
+        r = _half(lib, n, "fp32", batch=3)
+        r.restore(ck)
+        r.step(20)
+        for x, y in zip(r.get_state(), (a, b)):
+            assert np.array_equal(x, y)
+        # replace field 1 mid-run: the other fields are untouched
+        g.set_field(1, u0[0], v0[0])
+        g.step(5)
+        res.append(g.get_state())
+    for x, y in zip(res[0], res[1]):
+        assert np.array_equal(x, y)
