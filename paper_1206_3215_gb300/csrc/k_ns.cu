@@ -58,7 +58,9 @@ template <class Rl>
 cudaError_t ns_row_pass(V2<Rl> *c1, V2<Rl> *c2, const void *fs, int64_t nx, int64_t ny, int64_t batch,
                         const TW<Rl> *twx, cudaStream_t s)
 {
-    return launch_row<Rl>(nx, NsRow<Rl>{c1, c2, static_cast<const NsField *>(fs), ny}, twx, batch * ny, s);
+    int lgy = 0;
+    while ((int64_t(1) << lgy) < ny) ++lgy;  // ny is a power of two
+    return launch_row<Rl>(nx, NsRow<Rl>{c1, c2, static_cast<const NsField *>(fs), lgy}, twx, batch * ny, s);
 }
 
 template <class Rl>

@@ -175,8 +175,17 @@ template <class Rl, int N, int NIN, bool LEAN = false, int PMAX = 32> struct Col
     static constexpr int MIN_CTAS = LEAN ? (THREADS * Shape<Rl>::MIN_CTAS <= 512 ? Shape<Rl>::MIN_CTAS : 1) : 1;
 };
 
-template <class Rl, int N, class Op> using RowCfgOf = RowCfg<Rl, N, Op::NIN, Op::LEAN, Op::PMAX>;
-template <class Rl, int N, class Op> using ColCfgOf = ColCfg<Rl, N, Op::NIN, Op::LEAN, Op::PMAX>;
+// points per thread an op allows at length N: Op::pmax(N) where the op
+// defines it, else Op::PMAX
+template <class Op, class = void> struct HasPmaxN : std::false_type {};
+template <class Op> struct HasPmaxN<Op, std::void_t<decltype(Op::pmax(1))>> : std::true_type {};
+template <class Op> __host__ __device__ constexpr int op_pmax(int n)
+{
+    if constexpr (HasPmaxN<Op>::value) return Op::pmax(n);
+    else return Op::PMAX;
+}
+template <class Rl, int N, class Op> using RowCfgOf = RowCfg<Rl, N, Op::NIN, Op::LEAN, op_pmax<Op>(N)>;
+template <class Rl, int N, class Op> using ColCfgOf = ColCfg<Rl, N, Op::NIN, Op::LEAN, op_pmax<Op>(N)>;
 
 // ----------------------------------------------------------------------------
 // cp.async: per-thread asynchronous global -> shared copies (no registers held)
