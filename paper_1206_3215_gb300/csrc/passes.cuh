@@ -58,6 +58,9 @@ namespace pss {
 #ifndef PSS_COL_THREADS
 #define PSS_COL_THREADS 256
 #endif
+#ifndef PSS_ROW_THREADS_SMALL
+#define PSS_ROW_THREADS_SMALL 64
+#endif
 #ifndef PSS_COL_WIDE_THREADS
 #define PSS_COL_WIDE_THREADS 512
 #endif
@@ -142,7 +145,10 @@ __host__ __device__ constexpr int col_stride(int base, int W, int ESZ)
 template <class Rl, int N, int NIN, bool LEAN = false, int PMAX = 32> struct RowCfg {
     static constexpr int P = Shape<Rl>::rowP(N) < PMAX ? Shape<Rl>::rowP(N) : PMAX;
     static constexpr int T = N / P;
-    static constexpr int ROWS = T >= PSS_ROW_THREADS ? 1 : PSS_ROW_THREADS / T;  // ~256 threads per CTA
+    // ~256 threads per CTA; small rows (N <= 256) take ~64 so that a batch of
+    // small grids still spreads over many SMs (a 128^2 field is 2 CTAs, not 1/2)
+    static constexpr int RT = N <= 256 ? PSS_ROW_THREADS_SMALL : PSS_ROW_THREADS;
+    static constexpr int ROWS = T >= RT ? 1 : RT / T;
     static constexpr int PADLOG = pad_log(P);
     static constexpr int LINE = N + (N >> PADLOG);
     static constexpr int THREADS = ROWS * T;

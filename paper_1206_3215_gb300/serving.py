@@ -12,6 +12,10 @@ does not wait for the whole batch to finish).  A new pool is created only
 when the device has room for it (free memory minus a reserve); otherwise the
 request waits, and idle empty pools are released to make room.
 
+A pool of N x N grids has min(slots, pool_points / N^2) slots: small grids
+are batched to fill the GPU, while a 2048^2 field, which fills it alone,
+does not wait for the steps of seven others.
+
 Every field evolves exactly as it would alone: a batch does not couple its
 fields (sine-Gordon and Navier-Stokes give bit-identical fields; the NLS
 split-step merges the half steps inside one pss_step_n call, so a solve cut
@@ -30,8 +34,10 @@ import numpy as np
 
 from . import Grid, pss_step_n
 
+# device bytes per grid point of one slot (complex work arrays; sine-Gordon
+# counts the half-spectrum copies as well)
 BYTES_PER_POINT = {("nls", "fp32"): 3 * 8, ("nls", "fp64"): 3 * 16,
-                   ("sg", "fp32"): 5 * 8, ("sg", "fp64"): 5 * 16,
+                   ("sg", "fp32"): 7 * 8, ("sg", "fp64"): 7 * 16,
                    ("ns", "fp32"): 7 * 8, ("ns", "fp64"): 7 * 16}
 
 
@@ -96,8 +102,12 @@ class Server:
     """Admits, batches and advances requests; see the module docstring."""
 
     def __init__(self, slots: int = 8, round_max: int = 50, reserve_bytes: int = 2 << 30,
-                 max_pools: int = 64):
+                 max_pools: int = 64, pool_points: int = 1 << 22):
+        # a pool of N x N grids gets min(slots, pool_points / N^2) slots (at
+        # least 1): one 2048^2 field already fills the GPU, and batching more of
+        # them only makes each request wait for the others' steps
         self.slots = slots
+        self.pool_points = pool_points
         self.round_max = round_max
         self.reserve = reserve_bytes
         self.max_pools = max_pools
@@ -106,10 +116,14 @@ class Server:
         self.rounds = 0
         self.point_steps = 0
 
+    def _slots_for(self, key) -> int:
+        n = key[1]
+        return max(1, min(self.slots, self.pool_points // (n * n)))
+
     # -- memory admission --------------------------------------------------
     def _pool_bytes(self, key):
         eq, n, precision, _ = key
-        return BYTES_PER_POINT[(eq, precision)] * n * n * self.slots + (4 << 20)
+        return BYTES_PER_POINT[(eq, precision)] * n * n * self._slots_for(key) + (4 << 20)
 
     def _room_for(self, key) -> bool:
         import torch
@@ -131,7 +145,7 @@ class Server:
         while not self._room_for(key):
             if not self._release_idle():
                 return None
-        p = Pool(key, self.slots)
+        p = Pool(key, self._slots_for(key))
         self.pools[key] = p
         return p
 

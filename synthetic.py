@@ -123,7 +123,7 @@ def serving_mix(count: int, rate_hz: float, sizes=(128, 256, 512, 1024, 2048), s
             params = {"dt": 1e-3, "lx": 20 * math.pi, "ly": 20 * math.pi}
         elif eq == "sg":
             state = sg_gaussian(n, seed=fseed)
-            params = {"dt": 1e-3, "lx": 10 * math.pi, "ly": 10 * math.pi}
+            params = {"dt": 1e-3, "lx": 10 * math.pi, "ly": 10 * math.pi, "rfft": 1}
         else:
             state = (ns_power_law(n, seed=fseed),)
             params = {"dt": 2.5e-4, "lx": 2 * math.pi, "ly": 2 * math.pi, "nu": 1e-3}
