@@ -502,7 +502,7 @@ def run_ours(args):
         serve = {"requests": st["requests"], "arrival_rate_hz": 40.0, "p50_latency_ms": st["p50_latency_s"] * 1e3,
                  "p99_latency_ms": st["p99_latency_s"] * 1e3, "throughput_gpt_steps_s": st["gpt_steps_per_s"],
                  "wall_s": st["wall_s"], "pools": st["pools"], "rounds": st["rounds"],
-                 "mix": "NLS/SG/NS FP32, N in {128,256,512,1024,2048}, 50-500 steps, 8 slots per pool"}
+                 "mix": "NLS/SG/NS FP32, N in {128,256,512,1024,2048}, 50-500 steps, min(8, 2^22/N^2) slots per pool"}
 
     other = None if args.no_other else other_paths(stream, rank)
 

@@ -590,14 +590,14 @@ template <class Rl> int ns_update(pss_grid *g, bool in_graph)
     int rc;
     if (!in_graph && (rc = g->pass_begin(0))) return rc;
     cudaError_t e = ns_row_pass<Rl>(B<Rl>(g, 4), B<Rl>(g, 5), g->ns_field, g->nx, g->ny, g->batch,
-                                    Tw<Rl>(g->twx), g->stream);
+                                    Tw<Rl>(g->twx), g->stream, g->p.dealias != 0);
     if ((!in_graph && (rc = g->pass_end())) || (rc = g->cuda(e, "ns row pass"))) return rc;
     int groups = 0;
     if (!in_graph && (rc = g->pass_begin(1))) return rc;
     e = ns_col_pass<Rl>(B<Rl>(g, 4), B<Rl>(g, 5), w, B<Rl>(g, 3), g->ns_field, g->partials, Rt<Rl>(g->kxo),
                         Rt<Rl>(g->kyo), Rt<Rl>(g->kx2), Rt<Rl>(g->ky2), Rt<Rl>(g->keepx), Rt<Rl>(g->keepy), g->p.dt,
                         g->p.nu, g->nx, g->ny, g->batch, ctl, g->p.scheme == PSS_NS_MIDPOINT ? 1 : 0, Tw<Rl>(g->twy),
-                        &groups, g->stream);
+                        &groups, g->stream, g->p.dealias != 0);
     if ((!in_graph && (rc = g->pass_end())) || (rc = g->cuda(e, "ns column pass"))) return rc;
     if (!in_graph && (rc = g->pass_begin(2))) return rc;
     e = ns_decide(g->ns_field, g->partials, groups, g->batch, ctl, parseval, g->p.tol, g->p.max_iter, g->stream);

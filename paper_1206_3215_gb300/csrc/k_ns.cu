@@ -56,23 +56,25 @@ __global__ void k_ns_advance(int *ctl, int use_graph, cudaGraphConditionalHandle
 
 template <class Rl>
 cudaError_t ns_row_pass(V2<Rl> *c1, V2<Rl> *c2, const void *fs, int64_t nx, int64_t ny, int64_t batch,
-                        const TW<Rl> *twx, cudaStream_t s)
+                        const TW<Rl> *twx, cudaStream_t s, bool dealias)
 {
     int lgy = 0;
     while ((int64_t(1) << lgy) < ny) ++lgy;  // ny is a power of two
-    return launch_row<Rl>(nx, NsRow<Rl>{c1, c2, static_cast<const NsField *>(fs), lgy}, twx, batch * ny, s);
+    return launch_row<Rl>(nx, NsRow<Rl>{c1, c2, static_cast<const NsField *>(fs), lgy, dealias ? 1 : 0}, twx,
+                          batch * ny, s);
 }
 
 template <class Rl>
 cudaError_t ns_col_pass(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, void *fs, double *partials,
                         const Rl *kxo, const Rl *kyo, const Rl *kx2, const Rl *ky2, const Rl *keepx,
                         const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch,
-                        const int *ctl, int midpoint, const TW<Rl> *twy, int *groups_out, cudaStream_t s)
+                        const int *ctl, int midpoint, const TW<Rl> *twy, int *groups_out, cudaStream_t s,
+                        bool dealias)
 {
     return midpoint ? ns_col_mid<Rl>(c1, c2, w, jn, fs, partials, kxo, kyo, kx2, ky2, keepx, keepy, dt, nu, nx, ny,
-                                     batch, ctl, twy, groups_out, s)
+                                     batch, ctl, twy, groups_out, s, dealias)
                     : ns_col_run<Rl, false>(c1, c2, w, jn, fs, partials, kxo, kyo, kx2, ky2, keepx, keepy, dt, nu,
-                                            nx, ny, batch, ctl, twy, groups_out, s);
+                                            nx, ny, batch, ctl, twy, groups_out, s, dealias);
 }
 
 template <class Rl>
@@ -109,11 +111,11 @@ size_t ns_field_bytes() { return sizeof(NsField); }
 
 #define PSS_INST(Rl)                                                                                         \
     template cudaError_t ns_row_pass<Rl>(V2<Rl> *, V2<Rl> *, const void *, int64_t, int64_t, int64_t,       \
-                                         const TW<Rl> *, cudaStream_t);                                      \
+                                         const TW<Rl> *, cudaStream_t, bool);                                \
     template cudaError_t ns_col_pass<Rl>(V2<Rl> *, V2<Rl> *, V2<Rl> *const[3], V2<Rl> *, void *, double *,  \
                                          const Rl *, const Rl *, const Rl *, const Rl *, const Rl *,         \
                                          const Rl *, double, double, int64_t, int64_t, int64_t,             \
-                                         const int *, int, const TW<Rl> *, int *, cudaStream_t);            \
+                                         const int *, int, const TW<Rl> *, int *, cudaStream_t, bool);      \
     template cudaError_t ns_prep_pass<Rl>(V2<Rl> *const[3], const void *, V2<Rl> *, V2<Rl> *, const Rl *,     \
                                           const Rl *,                                                         \
                                           const Rl *, const Rl *, int64_t, int64_t, int64_t, const TW<Rl> *, \

@@ -83,7 +83,9 @@ template <class Rl> struct NsRow {
     static constexpr int PMAX = 16;
     V2<Rl> *c1, *c2;  // in: C1, C2 rows; out: row transform of J into c1
     const NsField *fs;
-    int lgy;  // log2 ny: row r belongs to field r >> lgy
+    int lgy;      // log2 ny: row r belongs to field r >> lgy
+    int dealias;  // 2/3 rule: columns with 3 |mx| >= nx are not written (they stay
+                  // zero: the column pass skips them and the mask discards J there)
     __device__ const V2<Rl> *in(int k) const { return k == 0 ? c1 : c2; }
     template <int N, int P, bool BLOCK, class Sm>
     __device__ __forceinline__ void row(V2<Rl> (&v)[2][P], int64_t r, bool ok, int t, const Sm (&sm)[2],
@@ -98,7 +100,14 @@ template <class Rl> struct NsRow {
         fence(v[0]);
         block_fft<N, P, -1, BLOCK>(v[0], sm[0], t, tw);
         const bool live = ok && fs[r >> lgy].active;
-        store_line<P, N / P>(v[0], c1 + r * N, 1, t, live);
+        constexpr int T = N / P;
+        V2<Rl> *p = c1 + r * N + t;
+#pragma unroll
+        for (int m = 0; m < P; ++m, p += T) {
+            const int x = t + T * m;
+            const bool kept = !dealias || 3 * (x < N / 2 ? x : N - x) < N;
+            if (live && kept) *p = v[0][m];
+        }
     }
 };
 
@@ -117,6 +126,10 @@ template <class Rl, bool MID> struct NsCol {
     int64_t nx;
     const int *kptr;  // fixed-point update index of this pass (device, set by k_ns_advance)
     int W;
+    // 2/3 rule: column groups skip_lo .. skip_lo + skip_n - 1 hold only modes
+    // with 3|mx| >= nx, which the mask keeps at zero in w, J and the
+    // derivative fields; the pass does not visit them (0, 0 without dealiasing)
+    int64_t skip_lo, skip_n;
     static constexpr bool midpoint = MID;  // implicit midpoint, else trapezoidal Jacobian
     __device__ const V2<Rl> *in(int) const { return c1; }
     __device__ V2<Rl> *wb(int b) const { return b == 0 ? w0 : b == 1 ? w1 : w2; }
@@ -197,7 +210,8 @@ template <class Rl, bool MID> struct NsCol {
             }
         }
         // FP64 partial of |w^{k+1} - w^k|^2 over this tile, folded in a fixed order
-        block_partial(acc, partials + field * (nx / W) + x / W);
+        const int64_t g = x / W;
+        block_partial(acc, partials + field * (nx / W - skip_n) + (g < skip_lo ? g : g - skip_n));
     }
     // sum over the CTA (all threads of the tile) in a fixed tree; thread 0 writes
     __device__ __forceinline__ void block_partial(double acc, double *out) const
@@ -266,19 +280,39 @@ template <class Rl> struct NsPrep {
 };
 
 // column pass of one fixed-point update (scheme chosen by MID)
+// the run of column groups (w columns each) whose every column has
+// 3 |mx| >= nx: storage columns x with mx = x (x < nx/2) or x - nx
+inline void ns_masked_groups(int64_t nx, int w, int64_t *lo, int64_t *n)
+{
+    auto masked = [nx](int64_t x) { return 3 * (x < nx / 2 ? x : nx - x) >= nx; };
+    int64_t first = -1, last = -1;
+    for (int64_t g = 0; g < nx / w; ++g) {
+        bool all = true;
+        for (int64_t x = g * w; x < (g + 1) * w; ++x) all = all && masked(x);
+        if (all) {
+            if (first < 0) first = g;
+            last = g;
+        }
+    }
+    *lo = first < 0 ? 0 : first;
+    *n = first < 0 ? 0 : last - first + 1;
+}
+
 template <class Rl, bool MID>
 cudaError_t ns_col_run(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, void *fs, double *partials,
                         const Rl *kxo, const Rl *kyo, const Rl *kx2, const Rl *ky2, const Rl *keepx,
                         const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch,
-                        const int *ctl, const TW<Rl> *twy, int *groups_out, cudaStream_t s)
+                        const int *ctl, const TW<Rl> *twy, int *groups_out, cudaStream_t s, bool dealias)
 {
     NsCol<Rl, MID> op{c1, c2, w[0], w[1], w[2], jn, static_cast<NsField *>(fs), partials, kxo, kyo, kx2, ky2,
-                 keepx, keepy, Rl(0.5 * dt), Rl(0.5 * dt * nu), Rl(1.0 / (double(nx) * double(ny))), nx, ctl, 0};
+                 keepx, keepy, Rl(0.5 * dt), Rl(0.5 * dt * nu), Rl(1.0 / (double(nx) * double(ny))), nx, ctl, 0,
+                 0, 0};
     switch (ny) {
-#define PSS_CASE(N)                                         \
-    case N:                                                 \
-        op.W = ColCfgOf<Rl, N, NsCol<Rl, MID>>::W;                         \
-        *groups_out = int(nx / ColCfgOf<Rl, N, NsCol<Rl, MID>>::W);        \
+#define PSS_CASE(N)                                                                   \
+    case N:                                                                           \
+        op.W = ColCfgOf<Rl, N, NsCol<Rl, MID>>::W;                                    \
+        if (dealias) ns_masked_groups(nx, op.W, &op.skip_lo, &op.skip_n);             \
+        *groups_out = int(nx / op.W - op.skip_n);                                     \
         return launch_col_n<Rl, N>(op, twy, nx, batch, s);
         PSS_FOR_EACH_N(PSS_CASE)
 #undef PSS_CASE
@@ -291,6 +325,6 @@ template <class Rl>
 cudaError_t ns_col_mid(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, void *fs, double *partials,
                        const Rl *kxo, const Rl *kyo, const Rl *kx2, const Rl *ky2, const Rl *keepx,
                        const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch,
-                       const int *ctl, const TW<Rl> *twy, int *groups_out, cudaStream_t s);
+                       const int *ctl, const TW<Rl> *twy, int *groups_out, cudaStream_t s, bool dealias);
 
 }  // namespace pss

@@ -75,7 +75,7 @@ inline cudaError_t launch_col_n(Op op, const TW<Rl> *tw, int64_t nx, int64_t bat
     static int ctas[32] = {};
     cudaError_t e = allow_smem(k, C::SMEM, done);
     if (e != cudaSuccess) return e;
-    const int64_t tiles = (nx / C::W) * batch;
+    const int64_t tiles = kept_groups(op, nx / C::W) * batch;
     if (tiles <= 0) return cudaSuccess;
     int grid = 0;
     if ((e = resident_ctas(k, C::THREADS, C::SMEM, ctas, &grid)) != cudaSuccess) return e;

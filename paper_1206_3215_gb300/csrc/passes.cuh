@@ -291,7 +291,24 @@ template <class Op> __device__ __forceinline__ auto col_in(const Op &op, int k, 
     else return op.in(k);
 }
 
-// tiles: (NX / W) column groups per field, fields in order
+// Column groups a column op visits: all nx / W of them, or, where the op
+// defines skip_lo / skip_n, all but the skip_n groups from skip_lo on (a
+// contiguous run the op knows to be zero and to stay zero).
+template <class Op, class = void> struct SkipsGroups : std::false_type {};
+template <class Op>
+struct SkipsGroups<Op, std::void_t<decltype(std::declval<const Op &>().skip_n)>> : std::true_type {};
+template <class Op> __host__ __device__ __forceinline__ int64_t kept_groups(const Op &op, int64_t groups)
+{
+    if constexpr (SkipsGroups<Op>::value) return groups - op.skip_n;
+    else return groups;
+}
+template <class Op> __host__ __device__ __forceinline__ int64_t group_index(const Op &op, int64_t g)
+{
+    if constexpr (SkipsGroups<Op>::value) return g < op.skip_lo ? g : g + op.skip_n;
+    else return g;
+}
+
+// tiles: (NX / W) column groups per field (fewer where the op skips some), fields in order
 template <class Rl, int N, class Op>
 __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op>::THREADS, ColCfgOf<Rl, N, Op>::MIN_CTAS)
     k_col(Op op, const TW<Rl> *__restrict__ tw, int64_t nx, int64_t batch)
@@ -303,12 +320,12 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op>::THREADS, ColCfgOf<Rl, N, 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *const buf = reinterpret_cast<V *>(smem_raw);
     const int c = threadIdx.x % C::W, t = threadIdx.x / C::W;
-    const int64_t groups = nx / C::W, tiles = groups * batch;
+    const int64_t groups = kept_groups(op, nx / C::W), tiles = groups * batch;
 
     auto line = [&](int b, int k) { return Sm{buf + b * C::BUF + (k * C::W + c) * C::STRIDE}; };
     auto issue = [&](int64_t tile, int b) {
         if (tile < tiles) {
-            const int64_t field = tile / groups, x = (tile % groups) * C::W + c;
+            const int64_t field = tile / groups, x = group_index(op, tile % groups) * C::W + c;
 #pragma unroll
             for (int k = 0; k < NIN; ++k)
                 stage_line<C::P, C::T>(line(b, k), col_in(op, k, field) + field * N * nx + x, nx, t);
@@ -329,7 +346,7 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op>::THREADS, ColCfgOf<Rl, N, 
             cp_async_wait<0>();
         }
         const int64_t field = tile / groups;
-        const int x = int((tile % groups) * C::W + c);
+        const int x = int(group_index(op, tile % groups) * C::W + c);
         V v[NIN][C::P];
         Sm sm[NIN];
 #pragma unroll
