@@ -129,6 +129,21 @@ int pss_set_state(pss_grid *g, const void *a, const void *b, int where);
  * call.  Errors: PSS_E_STATE (no state set), PSS_E_ARG (n < 0). */
 int pss_step_n(pss_grid *g, int64_t n);
 
+/* Sine-Gordon: set both time levels from u^n (a) and u^{n-1} (b), real
+ * [batch][ny][nx] in the grid's precision, instead of the start-up from
+ * u(0), u_t(0) of pss_set_state: uhat^n = F u^n, uhat^{n-1} = F u^{n-1}
+ * (e.g. to continue from two levels read back by pss_get_state; the exact
+ * bitwise resume is pss_checkpoint_*).  Resets the step counter.
+ * Errors: PSS_E_ARG (not a sine-Gordon grid, null pointer, bad location). */
+int pss_set_state_sg_levels(pss_grid *g, const void *u_n, const void *u_nm1, int where);
+
+/* Advance several grids in one call: grids[i] by n[i] >= 0 steps, each
+ * enqueued on its own grid's stream (grids on different streams run
+ * concurrently on the device).  Every grid is attempted; the return value is
+ * the first error, with that grid's message in pss_last_error(grids[i]).
+ * Errors: PSS_E_ARG (count < 0, null arrays or a null grid). */
+int pss_step_n_batch(pss_grid *const *grids, int count, const int64_t *n);
+
 /* Copy the state back (inverse of pss_set_state's layout).
  *  NLS: a = psi (complex).  SG: a = u^n, b = u^{n-1} (real; b may be NULL).
  *  NS:  a = omega^n (real).  Synchronises. */

@@ -28,7 +28,7 @@ EXPORTED = [
     "pss_conserved_quantities", "pss_stats", "pss_checkpoint_size", "pss_checkpoint_save",
     "pss_checkpoint_load", "pss_sync", "pss_destroy", "pss_last_error", "pss_fft2d",
     "pss_version", "pss_set_profiling", "pss_profile_read", "pss_nls_invariants_static",
-    "pss_set_field", "pss_get_field",
+    "pss_set_field", "pss_get_field", "pss_set_state_sg_levels", "pss_step_n_batch",
 ]
 
 
@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH):
             "pss_nls_invariants_static": (I, [P, P, I64, I64, I64, D, D, D, I, P, P]),
             "pss_set_field": (I, [P, I64, P, P, I]),
             "pss_get_field": (I, [P, I64, P, P, I]),
+            "pss_set_state_sg_levels": (I, [P, P, P, I]),
+            "pss_step_n_batch": (I, [P, I, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -124,6 +126,21 @@ def pss_set_state(h, a_ptr: int, b_ptr: int | None, where: int) -> None:
 
 def pss_step_n(h, n: int) -> None:
     _check(load_library().pss_step_n(h, n), h)
+
+
+def pss_set_state_sg_levels(h, un_ptr: int, unm1_ptr: int, where: int) -> None:
+    _check(load_library().pss_set_state_sg_levels(h, un_ptr, unm1_ptr, where), h)
+
+
+def pss_step_n_batch(handles, steps) -> None:
+    """Advance handles[i] by steps[i] steps (each on its own stream)."""
+    count = len(handles)
+    hs = (ctypes.c_void_p * max(count, 1))(*[h.value if hasattr(h, "value") else h for h in handles])
+    ns = (ctypes.c_int64 * max(count, 1))(*steps)
+    rc = load_library().pss_step_n_batch(hs, count, ns)
+    if rc != PSS_OK:
+        bad = next((h for h in handles if pss_last_error(h)), None)
+        raise PssError(rc, pss_last_error(bad) if bad is not None else "pss_step_n_batch failed")
 
 
 def pss_get_state(h, a_ptr: int, b_ptr: int | None, where: int) -> None:
@@ -270,6 +287,14 @@ class Grid:
         where = PSS_DEVICE if hasattr(a, "data_ptr") else PSS_HOST
         pss_set_state(self.h, pa, pb, where)
         self._keep = (ka, kb)  # device inputs must live until the copy ran
+
+    def set_levels(self, u_n, u_nm1):
+        """Sine-Gordon: both time levels u^n, u^{n-1} (arrays [batch][ny][nx])."""
+        ka, pa = self._prep(u_n, False)
+        kb, pb = self._prep(u_nm1, False)
+        where = PSS_DEVICE if hasattr(u_n, "data_ptr") else PSS_HOST
+        pss_set_state_sg_levels(self.h, pa, pb, where)
+        self._keep = (ka, kb)
 
     def step(self, n: int):
         pss_step_n(self.h, n)

@@ -193,6 +193,29 @@ int pss_step_n(pss_grid *g, int64_t n)
     return g->step_n(n);
 }
 
+int pss_set_state_sg_levels(pss_grid *g, const void *u_n, const void *u_nm1, int where)
+{
+    if (!g) return PSS_E_ARG;
+    if (g->p.eq != PSS_EQ_SG) return g->fail(PSS_E_ARG, "set_state_sg_levels: not a sine-Gordon grid");
+    if (!u_n || !u_nm1 || (where != PSS_HOST && where != PSS_DEVICE))
+        return g->fail(PSS_E_ARG, "set_state_sg_levels: null buffer or bad location");
+    DeviceGuard dg(g->dev);
+    return g->set_sg_levels(u_n, u_nm1, where);
+}
+
+int pss_step_n_batch(pss_grid *const *grids, int count, const int64_t *n)
+{
+    if (count < 0 || (count > 0 && (!grids || !n))) return PSS_E_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!grids[i]) return PSS_E_ARG;
+    int first = PSS_OK;
+    for (int i = 0; i < count; ++i) {
+        const int rc = pss_step_n(grids[i], n[i]);
+        if (rc != PSS_OK && first == PSS_OK) first = rc;
+    }
+    return first;
+}
+
 int pss_get_state(pss_grid *g, void *a, void *b, int where)
 {
     if (!g) return PSS_E_ARG;

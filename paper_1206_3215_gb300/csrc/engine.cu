@@ -409,6 +409,18 @@ template <class Rl> int sg_make_h(pss_grid *g)
     return g->cuda(fft_cols<Rl>(B<Rl>(g, 2), g->nx, g->ny, g->batch, +1, s, Tw<Rl>(g->twy), g->stream), "H");
 }
 
+// both levels from u^n, u^{n-1}: uhat^n = F u^n, d = uhat^n - F u^{n-1}
+template <class Rl> int sg_set_levels(pss_grid *g, const void *un, const void *unm1, int where)
+{
+    int rc;
+    if ((rc = load_real<Rl>(g, un, where, 3, 0, false)) || (rc = g->cuda(fft2<Rl>(g, B<Rl>(g, 0), -1), "forward")) ||
+        (rc = load_real<Rl>(g, unm1, where, 3, 1, false)) || (rc = g->cuda(fft2<Rl>(g, B<Rl>(g, 1), -1), "forward")) ||
+        (rc = g->cuda(cplx_axpy<Rl>(B<Rl>(g, 0), B<Rl>(g, 1), Rl(1), B<Rl>(g, 1), g->ntot, g->stream), "d")) ||
+        (rc = sg_make_h<Rl>(g)))
+        return rc;
+    return where == PSS_HOST ? g->cuda(cudaStreamSynchronize(g->stream), "sync") : PSS_OK;
+}
+
 // half spectra <-> full spectra of the sine-Gordon state
 template <class Rl> int sg_half_sync(pss_grid *g, bool to_half)
 {
@@ -854,6 +866,18 @@ int pss_grid::set_state(const void *a, const void *b, int where)
         half_valid = false;
     }
     return rc;
+}
+
+int pss_grid::set_sg_levels(const void *u_n, const void *u_nm1, int where)
+{
+    int rc = p.precision == PSS_FP32 ? sg_set_levels<float>(this, u_n, u_nm1, where)
+                                     : sg_set_levels<double>(this, u_n, u_nm1, where);
+    if (rc) return rc;
+    steps = 0;
+    has_state = true;
+    full_valid = true;
+    half_valid = false;
+    return PSS_OK;
 }
 
 int pss_grid::half_sync(bool to_half)

@@ -85,6 +85,7 @@ struct pss_grid {
 
     int init();
     int set_state(const void *a, const void *b, int where);
+    int set_sg_levels(const void *u_n, const void *u_nm1, int where);
     int step_n(int64_t n);
     int get_state(void *a, void *b, int where);
     int set_field(int64_t f, const void *a, const void *b, int where);

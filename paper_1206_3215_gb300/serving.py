@@ -32,7 +32,7 @@ from collections import deque
 
 import numpy as np
 
-from . import Grid, pss_step_n
+from . import Grid, pss_step_n_batch
 
 # device bytes per grid point of one slot (complex work arrays; sine-Gordon
 # counts the half-spectrum copies as well)
@@ -168,12 +168,17 @@ class Server:
 
     def _launch(self):
         import torch
+        ready = []
         for pool in self.pools.values():
             occ = pool.occupied()
             if pool.busy() or not occ:
                 continue
-            r = min(min(pool.slots[i][1] for i in occ), self.round_max)
-            pss_step_n(pool.grid.h, r)
+            ready.append((pool, min(min(pool.slots[i][1] for i in occ), self.round_max)))
+        if not ready:
+            return
+        # one call enqueues a round on every ready pool's stream
+        pss_step_n_batch([p.grid.h for p, _ in ready], [r for _, r in ready])
+        for pool, r in ready:
             ev = torch.cuda.Event()
             ev.record(pool.stream)
             pool.event = (ev, r)

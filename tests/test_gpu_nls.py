@@ -177,3 +177,21 @@ def test_errors_leave_handle_usable(lib, cuda_device):
     g.set_state(S.nls_gaussian(64)[None])
     g.step(2)
     assert np.isfinite(g.get_state()).all()
+
+
+def test_bench_configuration_fields_match_oracle(lib, orc, cuda_device):
+    # the benchmark's launch configuration: 32 fields of 1024^2 in one FP32
+    # batch.  Fields 0 and 31 after 20 steps against the oracle (sampled
+    # fields), and the mass of every field
+    n, B, dt, steps = 1024, 32, 1e-3, 20
+    f = S.nls_gaussian(n, seed=S.SEED_BASE + 1, batch=B)
+    g = _grid(lib, n, "fp32", batch=B, dt=dt)
+    g.set_state(f.astype(np.complex64))
+    m0 = g.conserved()[:, 0].copy()
+    g.step(steps)
+    got = g.get_state()
+    for i in (0, B - 1):
+        ref = orc.nls_run(f[i], L, L, dt, steps, merged=True)
+        assert rel_l2(got[i], ref) <= TOL32_STATE
+    m1 = g.conserved()[:, 0]
+    assert np.max(np.abs(m1 - m0) / m0) <= TOL32_MASS

@@ -71,3 +71,30 @@ def test_set_and_get_field_round_trip(lib, cuda_device):
         z = g.get_field(0)
         z = z[0] if isinstance(z, tuple) else z
         assert np.abs(z).max() == 0.0
+
+
+def test_step_n_batch_equals_separate_calls(lib, cuda_device):
+    # grids of different equations advanced by one pss_step_n_batch call
+    # equal the same grids advanced one call each, bit for bit
+    import math
+    def make():
+        g1 = lib.Grid("nls", 64, "fp32", dt=1e-3)
+        g1.set_state(S.nls_gaussian(64)[None])
+        g2 = lib.Grid("sg", 64, "fp32", lx=10 * math.pi, ly=10 * math.pi, dt=1e-3, rfft=1)
+        g2.set_state(*(a[None] for a in S.sg_gaussian(64)))
+        g3 = lib.Grid("ns", 64, "fp32", lx=2 * math.pi, ly=2 * math.pi, dt=2.5e-3, nu=1e-3)
+        g3.set_state(S.ns_power_law(64)[None])
+        return [g1, g2, g3]
+    a, b = make(), make()
+    lib.pss_step_n_batch([g.h for g in a], [7, 11, 5])
+    for g, k in zip(b, [7, 11, 5]):
+        g.step(k)
+    for ga, gb in zip(a, b):
+        ra, rb = ga.get_state(), gb.get_state()
+        ra = ra if isinstance(ra, tuple) else (ra,)
+        rb = rb if isinstance(rb, tuple) else (rb,)
+        for x, y in zip(ra, rb):
+            assert np.array_equal(x, y)
+        assert ga.stats() == gb.stats()
+    with pytest.raises(lib.PssError):
+        lib.pss_step_n_batch([a[0].h, a[1].h], [1, -1])

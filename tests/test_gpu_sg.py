@@ -226,3 +226,31 @@ def test_half_spectrum_batch_fields_resume_and_graphs(lib, cuda_device, monkeypa
         res.append(g.get_state())
     for x, y in zip(res[0], res[1]):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("rfft", [0, 1])
+def test_set_levels_continues_a_run(lib, cuda_device, rfft):
+    # pss_set_state_sg_levels: restart from the two levels read back by
+    # get_state; the continuation equals the uninterrupted run up to the
+    # rounding of the re-transformed levels
+    n, dt = 64, 1e-3
+    u0, v0 = S.sg_gaussian(n)
+    a = lib.Grid("sg", n, "fp64", lx=L, ly=L, x0=-L / 2, y0=-L / 2, dt=dt, rfft=rfft)
+    a.set_state(u0[None], v0[None])
+    a.step(30)
+    un, unm1 = a.get_state()
+    a.step(30)
+    b = lib.Grid("sg", n, "fp64", lx=L, ly=L, x0=-L / 2, y0=-L / 2, dt=dt, rfft=rfft)
+    b.set_levels(un, unm1)
+    assert b.stats()[0] == 0
+    b.step(30)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert rel_l2(y, x) <= 1e-12
+
+
+def test_set_levels_rejects_other_equations(lib, cuda_device):
+    g = lib.Grid("nls", 16, "fp32")
+    z = np.zeros((1, 16, 16), np.float32)
+    with pytest.raises(lib.PssError) as e:
+        g.set_levels(z, z)
+    assert e.value.code == lib.PSS_E_ARG
