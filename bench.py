@@ -263,6 +263,7 @@ def other_paths(stream, rank: int):
         u0, v0 = S.sg_gaussian(n, batch=B, seed=S.SEED_BASE + 2 + 100000 * rank)
         g = P.Grid("sg", n, prec, batch=B, lx=Ls, ly=Ls, dt=1e-3, stream=sc, rfft=rfft)
         g.set_state(u0, v0)
+        g.autotune(4)
         g.step(3)
         ms = timed_steps(g, K, stream)
         out[f"sg_2048_{prec}" + ("_half" if rfft else "")] = {"value": rate(B * n * n, ms), "unit": UNIT,
@@ -287,6 +288,7 @@ def other_paths(stream, rank: int):
     f = S.nls_gaussian(n, seed=S.SEED_BASE + 1 + 100000 * rank, batch=B).astype("complex64")
     g = P.Grid("nls", n, "fp32", batch=B, lx=L, ly=L, dt=DT, stream=sc)
     g.set_state(f)
+    g.autotune(4)
     g.step(3)
     P.pss_set_profiling(g.h, True)
     ms = timed_steps(g, K, stream)
@@ -380,6 +382,8 @@ def run_ours(args):
     g = P.Grid("nls", n, "fp32", batch=B, lx=L, ly=L, x0=-L / 2, y0=-L / 2, dt=DT,
                stream=stream.cuda_stream)
     g.set_state(psi0)
+    # plans: time both launch shapes on this grid (state restored), keep the faster
+    plans_changed = g.autotune(4)
     mass0 = g.conserved()[:, 0].copy()
 
     # warm-up
@@ -524,6 +528,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (state > 129 MB, streamed every pass)",
                        "parallelism": f"replicas x{world}"},
             "accuracy": {"mass_drift_max_rel": drift, "steps_run": total_steps},
+            "plans_changed_by_autotune": plans_changed,
             "fp64": fp64,
             "roofline": roofline,
             "cpu_baseline": cpu,

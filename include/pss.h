@@ -144,6 +144,21 @@ int pss_set_state_sg_levels(pss_grid *g, const void *u_n, const void *u_nm1, int
  * Errors: PSS_E_ARG (count < 0, null arrays or a null grid). */
 int pss_step_n_batch(pss_grid *const *grids, int count, const int64_t *n);
 
+/* Autotuner (plans).  The FP32 row and column pass kernels of length >= 512
+ * are compiled in two launch shapes: 32 points per thread with two CTAs per
+ * SM, and 16 points per thread with four.  pss_autotune times `steps` steps
+ * of this grid in each (on its current state, which is restored afterwards,
+ * step counter included) and records, per pass kernel, the faster one in a
+ * process-wide plan keyed by (equation, grid size, precision): every grid of
+ * that key then runs the same kernels, so batched and single runs stay equal.
+ * The shapes round differently (different transform factorisations), so a
+ * plan change alters results at the rounding level; cached step graphs are
+ * re-captured.  *changed receives the number of kernels whose plan changed.
+ * NLS and sine-Gordon FP32 grids only (others return 0 changes).  Setting the
+ * environment variable PSS_PLAN=0 or 1 pins every kernel to one shape.
+ * Errors: PSS_E_STATE (no state), PSS_E_OOM (no room for the state copy). */
+int pss_autotune(pss_grid *g, int steps, int *changed);
+
 /* Copy the state back (inverse of pss_set_state's layout).
  *  NLS: a = psi (complex).  SG: a = u^n, b = u^{n-1} (real; b may be NULL).
  *  NS:  a = omega^n (real).  Synchronises. */

@@ -28,7 +28,7 @@ EXPORTED = [
     "pss_conserved_quantities", "pss_stats", "pss_checkpoint_size", "pss_checkpoint_save",
     "pss_checkpoint_load", "pss_sync", "pss_destroy", "pss_last_error", "pss_fft2d",
     "pss_version", "pss_set_profiling", "pss_profile_read", "pss_nls_invariants_static",
-    "pss_set_field", "pss_get_field", "pss_set_state_sg_levels", "pss_step_n_batch",
+    "pss_set_field", "pss_get_field", "pss_set_state_sg_levels", "pss_step_n_batch", "pss_autotune",
 ]
 
 
@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH):
             "pss_get_field": (I, [P, I64, P, P, I]),
             "pss_set_state_sg_levels": (I, [P, P, P, I]),
             "pss_step_n_batch": (I, [P, I, P]),
+            "pss_autotune": (I, [P, I, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -141,6 +142,13 @@ def pss_step_n_batch(handles, steps) -> None:
     if rc != PSS_OK:
         bad = next((h for h in handles if pss_last_error(h)), None)
         raise PssError(rc, pss_last_error(bad) if bad is not None else "pss_step_n_batch failed")
+
+
+def pss_autotune(h, steps: int = 4) -> int:
+    """Time both launch shapes on this grid's step; returns the kernels whose plan changed."""
+    c = ctypes.c_int()
+    _check(load_library().pss_autotune(h, steps, ctypes.byref(c)), h)
+    return c.value
 
 
 def pss_get_state(h, a_ptr: int, b_ptr: int | None, where: int) -> None:
@@ -295,6 +303,9 @@ class Grid:
         where = PSS_DEVICE if hasattr(u_n, "data_ptr") else PSS_HOST
         pss_set_state_sg_levels(self.h, pa, pb, where)
         self._keep = (ka, kb)
+
+    def autotune(self, steps: int = 4) -> int:
+        return pss_autotune(self.h, steps)
 
     def step(self, n: int):
         pss_step_n(self.h, n)

@@ -216,6 +216,14 @@ int pss_step_n_batch(pss_grid *const *grids, int count, const int64_t *n)
     return first;
 }
 
+int pss_autotune(pss_grid *g, int steps, int *changed)
+{
+    if (!g) return PSS_E_ARG;
+    if (!changed || steps < 1) return g->fail(PSS_E_ARG, "autotune: steps < 1 or null output");
+    DeviceGuard dg(g->dev);
+    return g->autotune(steps, changed);
+}
+
 int pss_get_state(pss_grid *g, void *a, void *b, int where)
 {
     if (!g) return PSS_E_ARG;

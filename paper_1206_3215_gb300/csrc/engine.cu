@@ -3,6 +3,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -10,6 +11,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "plan.h"
 #include "tables.h"
 
 using namespace pss;
@@ -179,9 +181,23 @@ int pss_grid::sync()
     return PSS_OK;
 }
 
+namespace pss {
+PlanTuning *plan_tuning()
+{
+    thread_local PlanTuning t;
+    return &t;
+}
+std::atomic<int> &plan_epoch()
+{
+    static std::atomic<int> e{0};
+    return e;
+}
+}  // namespace pss
+
 int pss_grid::pass_begin(int kind)
 {
     ++launches;
+    plan_tuning()->open_kind = kind;
     if (!profiling) return PSS_OK;
     while (ev_pool.size() < ev_used + 2) {
         cudaEvent_t e;
@@ -195,6 +211,7 @@ int pss_grid::pass_begin(int kind)
 
 int pss_grid::pass_end()
 {
+    plan_tuning()->open_kind = -1;
     if (!profiling) return PSS_OK;
     return cuda(cudaEventRecord(ev_pool[ev_used++], stream), "event record");
 }
@@ -893,6 +910,10 @@ int pss_grid::step_n(int64_t n)
 {
     if (n == 0) return PSS_OK;
     int rc;
+    if (graph_epoch != plan_epoch().load()) {  // a plan changed: recapture
+        drop_graphs();
+        graph_epoch = plan_epoch().load();
+    }
     if ((rc = half_sync(true))) return rc;
     if (half) full_valid = false;
 #define NLS(R) nls_step<R>(this, n)
@@ -1043,6 +1064,68 @@ int pss_grid::checkpoint(void *buf_, int where, bool save)
         full_valid = true;
         half_valid = false;
     }
+    return PSS_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Autotuner: time `steps` steps of this grid in each launch-shape variant
+// (on its own state, restored afterwards; a one-step round of each first, then
+// two alternating timed rounds, best of the two) and keep, per row and per
+// column pass kernel, the faster variant (variant 1 must win by more than 2 %).
+
+int pss_grid::autotune(int k, int *changed)
+{
+    *changed = 0;
+    if (p.precision != PSS_FP32 || p.eq == PSS_EQ_NS) return PSS_OK;  // nothing tunable
+    if (!has_state) return fail(PSS_E_STATE, "autotune before set_state");
+    void *save = nullptr;
+    const size_t bytes = checkpoint_bytes();
+    if (cudaMalloc(&save, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PSS_E_OOM, "autotune: no room for a copy of the state");
+    }
+    int rc = checkpoint(save, PSS_DEVICE, true);
+    const bool prof = profiling;
+    // per variant and pass kind, the best mean pass time over the rounds; round
+    // 0 (one step of each variant) only loads the kernels and warms the clocks
+    double t[2][2] = {{1e30, 1e30}, {1e30, 1e30}};
+    PlanTuning *pt = plan_tuning();
+    PlanSlot *used[2][8] = {};
+    int nused[2] = {0, 0};
+    for (int round = 0; round < 3 && rc == PSS_OK; ++round)
+        for (int v = 0; v < 2 && rc == PSS_OK; ++v) {
+            *pt = PlanTuning{};
+            pt->force = v;
+            drop_graphs();
+            if ((rc = profile_resolve())) break;
+            profiling = true;
+            for (int i = 0; i < 3; ++i) prof_ms[i] = 0, prof_n[i] = 0;
+            rc = step_n(round == 0 ? 1 : k);
+            if (!rc) rc = profile_resolve();
+            for (int kind = 0; kind < 2 && !rc && round > 0; ++kind)
+                if (prof_n[kind]) t[v][kind] = std::min(t[v][kind], prof_ms[kind] / prof_n[kind]);
+            if (v == 0 && round == 0)
+                for (int kind = 0; kind < 2; ++kind) {
+                    nused[kind] = pt->nused[kind];
+                    for (int i = 0; i < nused[kind]; ++i) used[kind][i] = pt->used[kind][i];
+                }
+            const int rrc = checkpoint(save, PSS_DEVICE, false);
+            if (!rc) rc = rrc;
+        }
+    *pt = PlanTuning{};
+    profiling = prof;
+    for (int i = 0; i < 3; ++i) prof_ms[i] = 0, prof_n[i] = 0;
+    cudaFree(save);
+    if (rc) return rc;
+    for (int kind = 0; kind < 2; ++kind)
+        for (int i = 0; i < nused[kind]; ++i) {
+            const int pick = t[1][kind] < 0.98 * t[0][kind] ? 1 : 0;
+            const int old = used[kind][i]->var.exchange(pick);
+            if ((old < 0 ? 0 : old) != pick) ++*changed;  // an unset slot ran variant 0
+        }
+    if (*changed) plan_epoch().fetch_add(1);
+    drop_graphs();
+    graph_epoch = plan_epoch().load();
     return PSS_OK;
 }
 

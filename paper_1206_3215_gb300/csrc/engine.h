@@ -73,6 +73,17 @@ struct pss_grid {
     cudaGraphExec_t ns_exec = nullptr;
     cudaGraphConditionalHandle ns_cond = 0;
     std::vector<std::pair<int64_t, cudaGraphExec_t>> step_graphs;  // NLS/SG step_n(n), by n
+    int graph_epoch = 0;  // plan epoch the cached graphs were captured under
+    void drop_graphs()
+    {
+        if (ns_exec) cudaGraphExecDestroy(ns_exec);
+        if (ns_graph) cudaGraphDestroy(ns_graph);
+        for (auto &g : step_graphs) cudaGraphExecDestroy(g.second);
+        step_graphs.clear();
+        ns_exec = nullptr;
+        ns_graph = nullptr;
+    }
+    int autotune(int steps, int *changed);
 
     int64_t steps = 0;
     bool has_state = false;
@@ -99,12 +110,7 @@ struct pss_grid {
     {
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         ev_pool.clear();
-        if (ns_exec) cudaGraphExecDestroy(ns_exec);
-        if (ns_graph) cudaGraphDestroy(ns_graph);
-        for (auto &g : step_graphs) cudaGraphExecDestroy(g.second);
-        step_graphs.clear();
-        ns_exec = nullptr;
-        ns_graph = nullptr;
+        drop_graphs();
     }
     int check_ns_nonconv();
 

@@ -3,8 +3,10 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cstdlib>
 
 #include "passes.cuh"
+#include "plan.h"
 
 namespace pss {
 
@@ -48,11 +50,35 @@ template <class K> inline cudaError_t resident_ctas(K kernel, int threads, size_
     return cudaSuccess;
 }
 
-template <class Rl, int N, class Op>
-inline cudaError_t launch_row_n(Op op, const TW<Rl> *tw, int64_t rows_total, cudaStream_t s)
+template <class Rl, int N, class Op> constexpr bool tunable()
 {
-    using C = RowCfgOf<Rl, N, Op>;
-    auto k = k_row<Rl, N, Op>;
+    return sizeof(Rl) == 4 && Op::LEAN && N >= 512 && !SkipsGroups<Op>::value;
+}
+
+inline int plan_pick(PlanSlot &slot)
+{
+    PlanTuning *pt = plan_tuning();
+    if (pt->force >= 0) {
+        const int kind = pt->open_kind;
+        if (kind == 0 || kind == 1) {
+            bool seen = false;
+            for (int i = 0; i < pt->nused[kind]; ++i) seen = seen || pt->used[kind][i] == &slot;
+            if (!seen && pt->nused[kind] < 8) pt->used[kind][pt->nused[kind]++] = &slot;
+        }
+        return pt->force;
+    }
+    // PSS_PLAN=0|1 pins every tunable kernel to one variant (read per launch)
+    const char *e = getenv("PSS_PLAN");
+    if (e && (e[0] == '0' || e[0] == '1') && e[1] == 0) return e[0] - '0';
+    const int v = slot.var.load(std::memory_order_acquire);
+    return v < 0 ? 0 : v;
+}
+
+template <class Rl, int N, class Op, int VAR>
+inline cudaError_t launch_row_v(Op op, const TW<Rl> *tw, int64_t rows_total, cudaStream_t s)
+{
+    using C = RowCfgOf<Rl, N, Op, VAR>;
+    auto k = k_row<Rl, N, Op, VAR>;
     static std::atomic<unsigned> done{0};
     static int ctas[32] = {};
     cudaError_t e = allow_smem(k, C::SMEM, done);
@@ -66,11 +92,11 @@ inline cudaError_t launch_row_n(Op op, const TW<Rl> *tw, int64_t rows_total, cud
     return cudaGetLastError();
 }
 
-template <class Rl, int N, class Op>
-inline cudaError_t launch_col_n(Op op, const TW<Rl> *tw, int64_t nx, int64_t batch, cudaStream_t s)
+template <class Rl, int N, class Op, int VAR>
+inline cudaError_t launch_col_v(Op op, const TW<Rl> *tw, int64_t nx, int64_t batch, cudaStream_t s)
 {
-    using C = ColCfgOf<Rl, N, Op>;
-    auto k = k_col<Rl, N, Op>;
+    using C = ColCfgOf<Rl, N, Op, VAR>;
+    auto k = k_col<Rl, N, Op, VAR>;
     static std::atomic<unsigned> done{0};
     static int ctas[32] = {};
     cudaError_t e = allow_smem(k, C::SMEM, done);
@@ -82,6 +108,28 @@ inline cudaError_t launch_col_n(Op op, const TW<Rl> *tw, int64_t nx, int64_t bat
     if (tiles < grid) grid = int(tiles);
     k<<<dim3(unsigned(grid)), C::THREADS, C::SMEM, s>>>(op, tw, nx, batch);
     return cudaGetLastError();
+}
+
+template <class Rl, int N, class Op>
+inline cudaError_t launch_row_n(Op op, const TW<Rl> *tw, int64_t rows_total, cudaStream_t s)
+{
+    if constexpr (tunable<Rl, N, Op>()) {
+        static PlanSlot slot;
+        // every tile width divides the row stride: a variant choice needs no caller change
+        if (plan_pick(slot) == 1) return launch_row_v<Rl, N, Op, 1>(op, tw, rows_total, s);
+    }
+    return launch_row_v<Rl, N, Op, 0>(op, tw, rows_total, s);
+}
+
+template <class Rl, int N, class Op>
+inline cudaError_t launch_col_n(Op op, const TW<Rl> *tw, int64_t nx, int64_t batch, cudaStream_t s)
+{
+    if constexpr (tunable<Rl, N, Op>()) {
+        static PlanSlot slot;
+        if (nx % ColCfgOf<Rl, N, Op, 1>::W == 0 && plan_pick(slot) == 1)
+            return launch_col_v<Rl, N, Op, 1>(op, tw, nx, batch, s);
+    }
+    return launch_col_v<Rl, N, Op, 0>(op, tw, nx, batch, s);
 }
 
 // Row pass over every row of a [batch][ny][nx] array: transform length nx.

@@ -73,6 +73,9 @@ namespace pss {
 #ifndef PSS_MAX_NBUF
 #define PSS_MAX_NBUF 1
 #endif
+#ifndef PSS_THREADS_PER_SM
+#define PSS_THREADS_PER_SM 512
+#endif
 #ifndef PSS_MIN_CTAS64
 #define PSS_MIN_CTAS64 1
 #endif
@@ -110,6 +113,17 @@ template <class Rl> struct Shape {
     }
 };
 
+// Launch-shape variants a lean FP32 pass is compiled in (the plan the
+// autotuner picks from, per kernel instance): 0 = the shapes above (32 points
+// per thread, two CTAs of <= 128 registers per SM); 1 = 16 points per thread,
+// four CTAs per SM (<= 64 registers).
+template <class Rl, int VAR> struct VarShape {
+    static constexpr int PCAP = VAR == 1 ? 16 : 1 << 20;
+    static constexpr int CTAS = VAR == 1 ? 4 : Shape<Rl>::MIN_CTAS;
+    static constexpr int TPS = VAR == 1 ? 1024 : PSS_THREADS_PER_SM;
+};
+__host__ __device__ constexpr int imin(int a, int b) { return a < b ? a : b; }
+
 // dynamic shared memory a pass may use per CTA (the GB300 limit is 227 KB)
 constexpr size_t SMEM_LIMIT = 200 * 1024;
 
@@ -142,8 +156,9 @@ __host__ __device__ constexpr int col_stride(int base, int W, int ESZ)
 
 // LEAN: one shared-memory buffer and (FP32) two resident CTAs per SM, for ops
 // whose transforms fit in 128 registers; otherwise a double buffer, one CTA.
-template <class Rl, int N, int NIN, bool LEAN = false, int PMAX = 32> struct RowCfg {
-    static constexpr int P = Shape<Rl>::rowP(N) < PMAX ? Shape<Rl>::rowP(N) : PMAX;
+template <class Rl, int N, int NIN, bool LEAN = false, int PMAX = 32, int VAR = 0> struct RowCfg {
+    using VS = VarShape<Rl, VAR>;
+    static constexpr int P = imin(imin(Shape<Rl>::rowP(N), PMAX), VS::PCAP);
     static constexpr int T = N / P;
     // ~256 threads per CTA; small rows (N <= 256) take ~64 so that a batch of
     // small grids still spreads over many SMs (a 128^2 field is 2 CTAs, not 1/2)
@@ -158,13 +173,15 @@ template <class Rl, int N, int NIN, bool LEAN = false, int PMAX = 32> struct Row
     static constexpr int MAXB = LEAN ? Shape<Rl>::MAX_NBUF : 2;
     static constexpr int NBUF = (MAXB > 1 && size_t(2) * BUF * Shape<Rl>::ESZ <= SMEM_LIMIT) ? 2 : 1;
     static constexpr size_t SMEM = size_t(NBUF) * BUF * Shape<Rl>::ESZ;
-    // resident CTAs the registers are budgeted for: at most 512 threads per SM
-    // at 128 registers each
-    static constexpr int MIN_CTAS = LEAN ? (THREADS * Shape<Rl>::MIN_CTAS <= 512 ? Shape<Rl>::MIN_CTAS : 1) : 1;
+    // resident CTAs the registers are budgeted for: at most VS::TPS threads
+    // per SM (512: 128 registers each)
+    static constexpr int MIN_CTAS =
+        LEAN ? (THREADS * VS::CTAS <= VS::TPS ? VS::CTAS : (VS::TPS / THREADS > 1 ? VS::TPS / THREADS : 1)) : 1;
 };
 
-template <class Rl, int N, int NIN, bool LEAN = false, int PMAX = 32> struct ColCfg {
-    static constexpr int P = Shape<Rl>::colP(N) < PMAX ? Shape<Rl>::colP(N) : PMAX;
+template <class Rl, int N, int NIN, bool LEAN = false, int PMAX = 32, int VAR = 0> struct ColCfg {
+    using VS = VarShape<Rl, VAR>;
+    static constexpr int P = imin(imin(Shape<Rl>::colP(N), PMAX), VS::PCAP);
     static constexpr int T = N / P;
     // lean ops (one buffer, <= 128 registers) may take the wide tiles
     static constexpr int W = LEAN ? Shape<Rl>::cols(N, P, NIN * Shape<Rl>::MAX_NBUF, true) : Shape<Rl>::cols(N, P);
@@ -176,9 +193,10 @@ template <class Rl, int N, int NIN, bool LEAN = false, int PMAX = 32> struct Col
     static constexpr int MAXB = LEAN ? Shape<Rl>::MAX_NBUF : 2;
     static constexpr int NBUF = (MAXB > 1 && size_t(2) * BUF * Shape<Rl>::ESZ <= SMEM_LIMIT) ? 2 : 1;
     static constexpr size_t SMEM = size_t(NBUF) * BUF * Shape<Rl>::ESZ;
-    // resident CTAs the registers are budgeted for: at most 512 threads per SM
-    // at 128 registers each
-    static constexpr int MIN_CTAS = LEAN ? (THREADS * Shape<Rl>::MIN_CTAS <= 512 ? Shape<Rl>::MIN_CTAS : 1) : 1;
+    // resident CTAs the registers are budgeted for: at most VS::TPS threads
+    // per SM (512: 128 registers each)
+    static constexpr int MIN_CTAS =
+        LEAN ? (THREADS * VS::CTAS <= VS::TPS ? VS::CTAS : (VS::TPS / THREADS > 1 ? VS::TPS / THREADS : 1)) : 1;
 };
 
 // points per thread an op allows at length N: Op::pmax(N) where the op
@@ -190,8 +208,10 @@ template <class Op> __host__ __device__ constexpr int op_pmax(int n)
     if constexpr (HasPmaxN<Op>::value) return Op::pmax(n);
     else return Op::PMAX;
 }
-template <class Rl, int N, class Op> using RowCfgOf = RowCfg<Rl, N, Op::NIN, Op::LEAN, op_pmax<Op>(N)>;
-template <class Rl, int N, class Op> using ColCfgOf = ColCfg<Rl, N, Op::NIN, Op::LEAN, op_pmax<Op>(N)>;
+template <class Rl, int N, class Op, int VAR = 0>
+using RowCfgOf = RowCfg<Rl, N, Op::NIN, Op::LEAN, op_pmax<Op>(N), VAR>;
+template <class Rl, int N, class Op, int VAR = 0>
+using ColCfgOf = ColCfg<Rl, N, Op::NIN, Op::LEAN, op_pmax<Op>(N), VAR>;
 
 // ----------------------------------------------------------------------------
 // cp.async: per-thread asynchronous global -> shared copies (no registers held)
@@ -232,11 +252,11 @@ __device__ __forceinline__ void read_line(V (&v)[P], const Sm &sm, int t)
 // Kernel shells
 
 // rows_total = batch * ny; row r of the batch starts at element r * NX
-template <class Rl, int N, class Op>
-__global__ void __launch_bounds__(RowCfgOf<Rl, N, Op>::THREADS, RowCfgOf<Rl, N, Op>::MIN_CTAS)
+template <class Rl, int N, class Op, int VAR>
+__global__ void __launch_bounds__(RowCfgOf<Rl, N, Op, VAR>::THREADS, RowCfgOf<Rl, N, Op, VAR>::MIN_CTAS)
     k_row(Op op, const TW<Rl> *__restrict__ tw, int64_t rows_total)
 {
-    using C = RowCfgOf<Rl, N, Op>;
+    using C = RowCfgOf<Rl, N, Op, VAR>;
     using V = V2<Rl>;
     using Sm = SmemLine<V, C::PADLOG>;
     constexpr int NIN = Op::NIN;
@@ -309,11 +329,11 @@ template <class Op> __host__ __device__ __forceinline__ int64_t group_index(cons
 }
 
 // tiles: (NX / W) column groups per field (fewer where the op skips some), fields in order
-template <class Rl, int N, class Op>
-__global__ void __launch_bounds__(ColCfgOf<Rl, N, Op>::THREADS, ColCfgOf<Rl, N, Op>::MIN_CTAS)
+template <class Rl, int N, class Op, int VAR>
+__global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, VAR>::THREADS, ColCfgOf<Rl, N, Op, VAR>::MIN_CTAS)
     k_col(Op op, const TW<Rl> *__restrict__ tw, int64_t nx, int64_t batch)
 {
-    using C = ColCfgOf<Rl, N, Op>;
+    using C = ColCfgOf<Rl, N, Op, VAR>;
     using V = V2<Rl>;
     using Sm = SmemLine<V, C::PADLOG>;
     constexpr int NIN = Op::NIN;

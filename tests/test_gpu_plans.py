@@ -1,0 +1,76 @@
+"""Plans and the autotuner: the second launch shape of the FP32 passes (16
+points per thread, four CTAs per SM) is as correct as the first, and tuning
+leaves the grid's state untouched and every grid of a key on one plan."""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as S
+from gpu_util import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+L = 20 * math.pi
+
+
+@pytest.mark.parametrize("plan", ["0", "1"])
+@pytest.mark.parametrize("n", [512, 1024])
+def test_each_shape_matches_oracle_nls(lib, orc, cuda_device, monkeypatch, plan, n):
+    monkeypatch.setenv("PSS_PLAN", plan)
+    dt, steps = 1e-3, 20
+    p0 = S.nls_gaussian(n)
+    g = lib.Grid("nls", n, "fp32", lx=L, ly=L, x0=-L / 2, y0=-L / 2, dt=dt)
+    g.set_state(p0[None])
+    g.step(steps)
+    ref = orc.nls_run(p0, L, L, dt, steps, merged=True)
+    assert rel_l2(g.get_state()[0], ref) <= 1e-5
+
+
+@pytest.mark.parametrize("plan", ["0", "1"])
+@pytest.mark.parametrize("rfft", [0, 1])
+def test_each_shape_matches_oracle_sg(lib, orc, cuda_device, monkeypatch, plan, rfft):
+    monkeypatch.setenv("PSS_PLAN", plan)
+    n, dt, steps, Ls = 1024, 1e-3, 20, 10 * math.pi
+    u0, v0 = S.sg_gaussian(n)
+    un, um = orc.sg_init(u0, v0, Ls, Ls, dt)
+    un, um = orc.sg_run(un, um, Ls, Ls, dt, steps)
+    ref, _ = orc.sg_fields(un, um)
+    g = lib.Grid("sg", n, "fp32", lx=Ls, ly=Ls, x0=-Ls / 2, y0=-Ls / 2, dt=dt, rfft=rfft)
+    g.set_state(u0[None], v0[None])
+    g.step(steps)
+    assert rel_l2(g.get_state()[0][0], ref) <= 2e-5
+
+
+@pytest.mark.parametrize("eq", ["nls", "sg"])
+def test_autotune_keeps_state_and_one_plan_per_key(lib, cuda_device, eq):
+    n = 512
+    if eq == "nls":
+        kw, state = dict(lx=L, ly=L, dt=1e-3), (S.nls_gaussian(n, batch=2),)
+    else:
+        kw, state = dict(lx=10 * math.pi, ly=10 * math.pi, dt=1e-3, rfft=1), S.sg_gaussian(n, batch=2)
+    g = lib.Grid(eq, n, "fp32", batch=2, **kw)
+    g.set_state(*state)
+    g.step(3)
+    before = g.get_state()
+    changed = g.autotune(3)
+    assert changed >= 0
+    after = g.get_state()
+    before = before if isinstance(before, tuple) else (before,)
+    after = after if isinstance(after, tuple) else (after,)
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    assert g.stats()[0] == 3
+    # the plan now in force is shared: a field run alone equals its slot
+    g2 = lib.Grid(eq, n, "fp32", batch=2, **kw)
+    g2.set_state(*state)
+    g2.step(8)
+    together = g2.get_state()
+    together = together if isinstance(together, tuple) else (together,)
+    h = lib.Grid(eq, n, "fp32", **kw)
+    h.set_state(*(s[1:2] for s in state))
+    h.step(8)
+    alone = h.get_state()
+    alone = alone if isinstance(alone, tuple) else (alone,)
+    for a, b in zip(alone, together):
+        assert np.array_equal(a[0], b[1])
