@@ -33,14 +33,19 @@ namespace pss {
 // live at a time: the column pass rebuilds the second derivative field from
 // the iterate it has just stored.  With every transform of a pass running
 // through one forward-FFT body (F^-1 x = conj(F conj x), exact) they fit the
-// lean shape (one buffer, <= 128 registers): 32 points per thread up to 1024
-// (two stages), 16 beyond (32 would spill with three stages).  Measured at
-// 4096^2 FP32: column pass 1.23 -> 0.82 ms per update.
+// lean shape (one buffer, <= 128 registers) with 32 points per thread (the
+// derivative pass takes 16 from 1024 on, where 32 spills).  Measured at
+// 4096^2 FP32: column pass 1.23 -> 0.82 ms per update in the lean shape with
+// 16 points, 0.54 -> 0.51 ms with 32 points (wider tiles) after the 2/3
+// pruning.
 #ifndef NS_PMAX
 #define NS_PMAX 32
 #endif
 #ifndef NS_PMAX_BIG
-#define NS_PMAX_BIG 16
+#define NS_PMAX_BIG 32
+#endif
+#ifndef NS_PREP_PMAX_BIG
+#define NS_PREP_PMAX_BIG 16
 #endif
 __host__ __device__ constexpr int ns_pmax(int n) { return n <= 1024 ? NS_PMAX : NS_PMAX_BIG; }
 #ifndef NS_LEAN
@@ -239,7 +244,7 @@ template <class Rl> struct NsPrep {
     static constexpr int NIN = 1;
     static constexpr bool LEAN = NS_LEAN;
     static constexpr int PMAX = NS_PMAX;
-    __host__ __device__ static constexpr int pmax(int n) { return n < 1024 ? NS_PMAX : NS_PMAX_BIG; }
+    __host__ __device__ static constexpr int pmax(int n) { return n < 1024 ? NS_PMAX : NS_PREP_PMAX_BIG; }
     const V2<Rl> *w0, *w1, *w2;
     const NsField *fs;
     V2<Rl> *c1, *c2;
