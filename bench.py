@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-other", action="store_true", help="skip the SG / NS / 4096^2 NLS lines")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--paper-tables", action="store_true",
                     help="replay the runs of Tables 2-4 instead (one JSON line with both timings)")
     ap.add_argument("--serve-requests", type=int, default=120)
@@ -154,7 +155,8 @@ def peaks():
 
 
 # files that define the NLS pass kernels (and their launch shapes)
-NLS_KERNEL_FILES = ("fft_core.cuh", "passes.cuh", "launch.cuh", "internal.h", "k_nls.cu")
+# sources the NLS pass kernels are compiled from (declarations-only headers excluded)
+NLS_KERNEL_FILES = ("fft_core.cuh", "passes.cuh", "launch.cuh", "k_nls.cu")
 
 
 def kernel_source_hash(files=NLS_KERNEL_FILES) -> str:
@@ -383,7 +385,7 @@ def run_ours(args):
                stream=stream.cuda_stream)
     g.set_state(psi0)
     # plans: time both launch shapes on this grid (state restored), keep the faster
-    plans_changed = g.autotune(4)
+    plans_changed = 0 if args.no_autotune else g.autotune(4)
     mass0 = g.conserved()[:, 0].copy()
 
     # warm-up
@@ -424,8 +426,10 @@ def run_ours(args):
     dom = "col" if cols_ms >= rows_ms else "row"
     dn, dms = (cols_n, cols_ms) if dom == "col" else (rows_n, rows_ms)
     achieved = bytes_per_pass / (dms / dn / 1e3) / 1e9 if dn else None
-    kernel_name = {"col": "k_col<float, 1024, NlsCol<float>>", "row": "k_row<float, 1024, NlsRow<float>>"}[dom]
-    traffic = ncu_traffic(kernel_name)
+    # launch shape 0 (the autotuner keeps it for these passes; if it changed
+    # a plan, the recorded counters are not for the kernels that ran)
+    kernel_name = {"col": "k_col<float, 1024, NlsCol<float>, 0>", "row": "k_row<float, 1024, NlsRow<float>, 0>"}[dom]
+    traffic = ncu_traffic(kernel_name) if plans_changed == 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                 "kernel": kernel_name, "peak_kind": peak_kind,
