@@ -280,19 +280,21 @@ def other_paths(stream, rank: int):
         out[f"sg_2048_{prec}" + ("_half" if rfft else "")] = {"value": rate(B * n * n, ms), "unit": UNIT,
                                                               "batch": B, "steps": K, "ms_per_step": ms}
         g.close()
-    # Navier-Stokes 4096^2, [0, 2 pi)^2, nu 1e-3, dt 2.5e-4, tol 1e-10, 2/3 rule
-    for scheme in ("cn", "midpoint"):
+    # Navier-Stokes 4096^2, [0, 2 pi)^2, nu 1e-3, dt 2.5e-4, tol 1e-10, 2/3 rule;
+    # both schemes, full and half spectra
+    for scheme, rfft in (("cn", 0), ("midpoint", 0), ("cn", 1), ("midpoint", 1)):
         n, Ln = 4096, 2 * math.pi
         g = P.Grid("ns", n, "fp32", lx=Ln, ly=Ln, dt=2.5e-4, nu=1e-3, tol=1e-10, dealias=1, scheme=scheme,
-                   stream=sc)
+                   rfft=rfft, stream=sc)
         g.set_state(S.ns_power_law(n, seed=S.SEED_BASE + 3 + 100000 * rank)[None])
         g.step(2)
         g.sync()
         u0 = g.stats()[1]
         K = 10
         ms = timed_steps(g, K, stream)
-        out[f"ns_4096_fp32_{scheme}"] = {"value": rate(n * n, ms), "unit": UNIT, "steps": K, "ms_per_step": ms,
-                                         "jacobians_per_step": (g.stats()[1] - u0) / K}
+        out[f"ns_4096_fp32_{scheme}" + ("_half" if rfft else "")] = {
+            "value": rate(n * n, ms), "unit": UNIT, "steps": K, "ms_per_step": ms,
+            "jacobians_per_step": (g.stats()[1] - u0) / K}
         g.close()
     # NLS at 4096^2 (2 fields, 256 MiB of state): the row/column pass roofline
     n, B, K = 4096, 2, 50

@@ -92,9 +92,11 @@ typedef struct pss_params {
     int32_t dealias;   /* NS: 1 = 2/3-rule square truncation (3|m| < n) on J and w0   */
     void *stream;      /* cudaStream_t to enqueue on, or NULL for a library stream    */
     int32_t scheme;    /* NS: PSS_NS_CN or PSS_NS_MIDPOINT                             */
-    int32_t rfft;      /* SG: 1 = step on half spectra (real-to-complex transforms,
-                          kx = 0 .. nx/2; Section 5.2's programs do the same);
-                          0 = full complex spectra.  Must be 0 for NLS and NS.     */
+    int32_t rfft;      /* SG, NS: 1 = keep the k-space state as half spectra
+                          (kx = 0 .. nx/2, the real fields' other half being its
+                          conjugate; the paper's programs used real-to-complex
+                          transforms for both, Sections 5.2-5.3); 0 = full complex
+                          spectra.  Must be 0 for NLS.                             */
 } pss_params;
 
 typedef struct pss_grid pss_grid;

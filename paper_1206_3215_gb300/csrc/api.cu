@@ -142,7 +142,7 @@ int pss_create_grid(pss_grid **out, const pss_params *p)
     else if (p->eq == PSS_EQ_NS && (!(p->nu >= 0) || !(p->tol > 0) || p->max_iter < 1)) bad = "nu/tol/max_iter";
     else if (p->scheme != PSS_NS_CN && p->scheme != PSS_NS_MIDPOINT) bad = "scheme";
     else if (p->rfft != 0 && p->rfft != 1) bad = "rfft (0 or 1)";
-    else if (p->rfft && p->eq != PSS_EQ_SG) bad = "rfft (sine-Gordon only)";
+    else if (p->rfft && p->eq == PSS_EQ_NLS) bad = "rfft (sine-Gordon and Navier-Stokes only)";
     if (bad) {
         g_create_error = std::string("invalid parameter: ") + bad;
         return PSS_E_ARG;

@@ -118,6 +118,10 @@ int pss_grid::init()
             (rc = upload_real<double>(this, kpx, &keepx)) || (rc = upload_real<double>(this, kpy, &keepy)))
             return rc;
     }
+    if (p.eq == PSS_EQ_NS && p.rfft) {
+        ns_half = true;
+        nsx = nx / 2 + 8;  // a multiple of every column-tile width
+    }
     if (p.eq == PSS_EQ_SG && p.rfft) {
         half = true;
         sx = nx / 2 + 8;  // a multiple of every column-tile width
@@ -576,16 +580,33 @@ template <class Rl> int ns_prep(pss_grid *g, bool per_step = false)
     ns_w<Rl>(g, w);
     return g->cuda(ns_prep_pass<Rl>(w, per_step ? g->ns_field : nullptr, B<Rl>(g, 4), B<Rl>(g, 5), Rt<Rl>(g->kxo),
                                     Rt<Rl>(g->kyo), Rt<Rl>(g->kx2), Rt<Rl>(g->ky2), g->nx, g->ny, g->batch,
-                                    Tw<Rl>(g->twy), g->stream), "ns derivatives");
+                                    Tw<Rl>(g->twy), g->stream, g->ns_half ? g->nsx : 0), "ns derivatives");
 }
+
+// offset of field f in a vorticity buffer (half spectra: rows of nsx)
+inline int64_t ns_off(const pss_grid *g, int64_t f) { return f * g->ny * (g->ns_half ? g->nsx : g->nx); }
 
 // derivatives of field f alone (its w^n in buffer 0)
 template <class Rl> int ns_prep_one(pss_grid *g, int64_t f)
 {
-    V2<Rl> *w[3] = {Bf<Rl>(g, 0, f), Bf<Rl>(g, 1, f), Bf<Rl>(g, 2, f)};
+    V2<Rl> *w[3] = {B<Rl>(g, 0) + ns_off(g, f), B<Rl>(g, 1) + ns_off(g, f), B<Rl>(g, 2) + ns_off(g, f)};
     return g->cuda(ns_prep_pass<Rl>(w, nullptr, Bf<Rl>(g, 4, f), Bf<Rl>(g, 5, f), Rt<Rl>(g->kxo), Rt<Rl>(g->kyo),
-                                    Rt<Rl>(g->kx2), Rt<Rl>(g->ky2), g->nx, g->ny, 1, Tw<Rl>(g->twy), g->stream),
+                                    Rt<Rl>(g->kx2), Rt<Rl>(g->ky2), g->nx, g->ny, 1, Tw<Rl>(g->twy), g->stream,
+                                    g->ns_half ? g->nsx : 0),
                    "ns derivatives");
+}
+
+// half spectra: the full spectra of `batch` fields at src into the vorticity
+// layout at dst (through buf[6] when src is buf[0] itself)
+template <class Rl> int ns_to_half(pss_grid *g, V2<Rl> *src, V2<Rl> *dst, int64_t batch)
+{
+    if (src == dst) {
+        const size_t hb = size_t(g->nsx) * size_t(g->ny) * size_t(batch) * g->esz;
+        int rc = g->cuda(pack_half<Rl>(src, B<Rl>(g, 6), g->nx, g->ny, g->nsx, batch, g->stream), "pack");
+        if (rc) return rc;
+        return g->cuda(cudaMemcpyAsync(dst, B<Rl>(g, 6), hb, cudaMemcpyDeviceToDevice, g->stream), "copy");
+    }
+    return g->cuda(pack_half<Rl>(src, dst, g->nx, g->ny, g->nsx, batch, g->stream), "pack");
 }
 
 // start of a step: mark every field active; the midpoint scheme also needs
@@ -604,7 +625,7 @@ template <class Rl> int ns_set(pss_grid *g, const void *w0, int where)
         (rc = g->cuda(apply_mask<Rl>(B<Rl>(g, 0), Rt<Rl>(g->keepx), Rt<Rl>(g->keepy), g->nx, g->ny, g->batch, g->stream),
                       "mask")) ||
         (rc = g->cuda(cudaMemsetAsync(g->ns_field, 0, size_t(g->batch) * ns_field_bytes(), g->stream), "memset")) ||
-        (rc = ns_prep<Rl>(g)))
+        (g->ns_half && (rc = ns_to_half<Rl>(g, B<Rl>(g, 0), B<Rl>(g, 0), g->batch))) || (rc = ns_prep<Rl>(g)))
         return rc;
     return where == PSS_HOST ? g->cuda(cudaStreamSynchronize(g->stream), "sync") : PSS_OK;
 }
@@ -619,14 +640,14 @@ template <class Rl> int ns_update(pss_grid *g, bool in_graph)
     int rc;
     if (!in_graph && (rc = g->pass_begin(0))) return rc;
     cudaError_t e = ns_row_pass<Rl>(B<Rl>(g, 4), B<Rl>(g, 5), g->ns_field, g->nx, g->ny, g->batch,
-                                    Tw<Rl>(g->twx), g->stream, g->p.dealias != 0);
+                                    Tw<Rl>(g->twx), g->stream, g->p.dealias != 0, g->ns_half);
     if ((!in_graph && (rc = g->pass_end())) || (rc = g->cuda(e, "ns row pass"))) return rc;
     int groups = 0;
     if (!in_graph && (rc = g->pass_begin(1))) return rc;
     e = ns_col_pass<Rl>(B<Rl>(g, 4), B<Rl>(g, 5), w, B<Rl>(g, 3), g->ns_field, g->partials, Rt<Rl>(g->kxo),
                         Rt<Rl>(g->kyo), Rt<Rl>(g->kx2), Rt<Rl>(g->ky2), Rt<Rl>(g->keepx), Rt<Rl>(g->keepy), g->p.dt,
                         g->p.nu, g->nx, g->ny, g->batch, ctl, g->p.scheme == PSS_NS_MIDPOINT ? 1 : 0, Tw<Rl>(g->twy),
-                        &groups, g->stream, g->p.dealias != 0);
+                        &groups, g->stream, g->p.dealias != 0, g->ns_half ? g->nsx : 0);
     if ((!in_graph && (rc = g->pass_end())) || (rc = g->cuda(e, "ns column pass"))) return rc;
     if (!in_graph && (rc = g->pass_begin(2))) return rc;
     e = ns_decide(g->ns_field, g->partials, groups, g->batch, ctl, parseval, g->p.tol, g->p.max_iter, g->stream);
@@ -714,12 +735,18 @@ template <class Rl> int ns_step(pss_grid *g, int64_t n)
     return rc;
 }
 
-// current vorticity of every field into buf[6]
+// current vorticity of every field into buf[6] (full spectra); half
+// spectra gather into buf[3] (J_hat^n, rebuilt at the start of every step)
+// and are extended to full width
 template <class Rl> int ns_current(pss_grid *g)
 {
     V2<Rl> *w[3];
     ns_w<Rl>(g, w);
-    return g->cuda(ns_gather<Rl>(g->ns_field, w, B<Rl>(g, 6), g->npts, g->batch, g->stream), "gather");
+    if (!g->ns_half)
+        return g->cuda(ns_gather<Rl>(g->ns_field, w, B<Rl>(g, 6), g->npts, g->batch, g->stream), "gather");
+    int rc = g->cuda(ns_gather<Rl>(g->ns_field, w, B<Rl>(g, 3), g->ny * g->nsx, g->batch, g->stream), "gather");
+    if (rc) return rc;
+    return g->cuda(unpack_half<Rl>(B<Rl>(g, 3), B<Rl>(g, 6), g->nx, g->ny, g->nsx, g->batch, g->stream), "unpack");
 }
 
 template <class Rl> int ns_get(pss_grid *g, void *a, int where)
@@ -736,6 +763,10 @@ template <class Rl> int ns_conserved(pss_grid *g, double *out)
     V2<Rl> *w[3];
     ns_w<Rl>(g, w);
     int rc;
+    if (g->ns_half) {  // sums over the full spectra of buf[6]
+        if ((rc = ns_current<Rl>(g))) return rc;
+        w[0] = w[1] = w[2] = B<Rl>(g, 6);
+    }
     if ((rc = g->cuda(ns_sums<Rl>(g->ns_field, w, g->nx, g->ny, g->batch, g->kx2d, g->ky2d, g->partials, g->sums,
                                   g->stream), "ns sums")) ||
         (rc = finish_sums(g)))
@@ -812,10 +843,14 @@ template <class Rl> int field_set(pss_grid *g, int64_t f, const void *a, const v
             (rc = g->cuda(fft_cols<Rl>(Bf<Rl>(g, 2, f), g->nx, g->ny, 1, +1, s, Tw<Rl>(g->twy), g->stream), "H")))
             return rc;
     } else {
-        if ((rc = load_real_one<Rl>(g, f, a, where, 6, 0, false)) ||
-            (rc = g->cuda(fft2_one<Rl>(g, Bf<Rl>(g, 0, f), -1), "forward")) ||
-            (rc = g->cuda(apply_mask<Rl>(Bf<Rl>(g, 0, f), Rt<Rl>(g->keepx), Rt<Rl>(g->keepy), g->nx, g->ny, 1,
+        // full spectrum of the field in buf[6] (half spectra) or buf[0], then
+        // (half spectra) into the field's slot of the half-width buffer 0
+        const int dst = g->ns_half ? 6 : 0;
+        if ((rc = load_real_one<Rl>(g, f, a, where, g->ns_half ? 3 : 6, dst, false)) ||
+            (rc = g->cuda(fft2_one<Rl>(g, Bf<Rl>(g, dst, f), -1), "forward")) ||
+            (rc = g->cuda(apply_mask<Rl>(Bf<Rl>(g, dst, f), Rt<Rl>(g->keepx), Rt<Rl>(g->keepy), g->nx, g->ny, 1,
                                          g->stream), "mask")) ||
+            (g->ns_half && (rc = ns_to_half<Rl>(g, Bf<Rl>(g, 6, f), B<Rl>(g, 0) + ns_off(g, f), 1))) ||
             (rc = g->cuda(cudaMemsetAsync(static_cast<char *>(g->ns_field) + f * ns_field_bytes(), 0, ns_field_bytes(),
                                           g->stream), "record")) ||
             (rc = ns_prep_one<Rl>(g, f)))
@@ -848,10 +883,17 @@ template <class Rl> int field_get(pss_grid *g, int64_t f, void *a, void *b, int 
             return rc;
     } else {
         V2<Rl> *w[3];
-        for (int i = 0; i < 3; ++i) w[i] = Bf<Rl>(g, i, f);  // field f's slot of each vorticity buffer
-        if ((rc = g->cuda(ns_gather<Rl>(static_cast<char *>(g->ns_field) + f * ns_field_bytes(), w, Bf<Rl>(g, 6, f),
-                                        g->npts, 1, g->stream), "gather")) ||
-            (rc = g->cuda(fft2_one<Rl>(g, Bf<Rl>(g, 6, f), +1), "inverse")) ||
+        for (int i = 0; i < 3; ++i) w[i] = B<Rl>(g, i) + ns_off(g, f);  // field f's slot of each vorticity buffer
+        const void *rec = static_cast<char *>(g->ns_field) + f * ns_field_bytes();
+        if (g->ns_half) {
+            V2<Rl> *h = B<Rl>(g, 3) + ns_off(g, f);
+            if ((rc = g->cuda(ns_gather<Rl>(rec, w, h, g->ny * g->nsx, 1, g->stream), "gather")) ||
+                (rc = g->cuda(unpack_half<Rl>(h, Bf<Rl>(g, 6, f), g->nx, g->ny, g->nsx, 1, g->stream), "unpack")))
+                return rc;
+        } else if ((rc = g->cuda(ns_gather<Rl>(rec, w, Bf<Rl>(g, 6, f), g->npts, 1, g->stream), "gather"))) {
+            return rc;
+        }
+        if ((rc = g->cuda(fft2_one<Rl>(g, Bf<Rl>(g, 6, f), +1), "inverse")) ||
             (rc = store_real_one<Rl>(g, f, Bf<Rl>(g, 6, f), a, where, 3)))
             return rc;
     }
@@ -1057,6 +1099,9 @@ int pss_grid::checkpoint(void *buf_, int where, bool save)
             for (int64_t i = 0; i < batch; ++i) h[i] = NsFieldHost{0, 0, 0, 0, i == 0 ? meta[1] : 0};
             rc = cuda(cudaMemcpyAsync(ns_field, h, size_t(batch) * ns_field_bytes(), cudaMemcpyHostToDevice, stream),
                       "fields");
+            if (!rc && ns_half)
+                rc = p.precision == PSS_FP32 ? ns_to_half<float>(this, B<float>(this, 0), B<float>(this, 0), batch)
+                                             : ns_to_half<double>(this, B<double>(this, 0), B<double>(this, 0), batch);
             if (!rc) rc = p.precision == PSS_FP32 ? ns_prep<float>(this) : ns_prep<double>(this);
         }
         if (rc || (rc = cuda(cudaStreamSynchronize(stream), "restore sync"))) return rc;

@@ -35,6 +35,11 @@ struct pss_grid {
     void *kx2h = nullptr;  // kx^2 of the half-spectrum columns (0 beyond nx/2)
     bool half_valid = false, full_valid = true;
     int half_sync(bool to_half);  // make the half (true) or full (false) copy current
+    // Navier-Stokes on half spectra (p.rfft): the vorticity iterates and
+    // J_hat^n in buf[0..3] hold [batch][ny][nsx] (kx = 0 .. nx/2); C1, C2 and
+    // the scratch buf[6] stay full width
+    bool ns_half = false;
+    int64_t nsx = 0;
 
     // tables (device)
     void *twx = nullptr, *twy = nullptr;                           // twiddles, precision

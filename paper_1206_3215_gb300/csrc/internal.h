@@ -70,17 +70,17 @@ cudaError_t unpack_half(const V2<Rl> *half, V2<Rl> *full, int64_t nx, int64_t ny
 size_t ns_field_bytes();  // bytes of the per-field fixed-point record
 template <class Rl>
 cudaError_t ns_row_pass(V2<Rl> *c1, V2<Rl> *c2, const void *fs, int64_t nx, int64_t ny, int64_t batch,
-                        const TW<Rl> *twx, cudaStream_t s, bool dealias);
+                        const TW<Rl> *twx, cudaStream_t s, bool dealias, bool half = false);
 template <class Rl>
 cudaError_t ns_col_pass(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, void *fs, double *partials,
                         const Rl *kxo, const Rl *kyo, const Rl *kx2, const Rl *ky2, const Rl *keepx,
                         const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch,
                         const int *ctl, int midpoint, const TW<Rl> *twy, int *groups_out, cudaStream_t s,
-                        bool dealias);
+                        bool dealias, int64_t sx = 0);
 template <class Rl>
 cudaError_t ns_prep_pass(V2<Rl> *const w[3], const void *fs, V2<Rl> *c1, V2<Rl> *c2, const Rl *kxo, const Rl *kyo,
                          const Rl *kx2, const Rl *ky2, int64_t nx, int64_t ny, int64_t batch,
-                         const TW<Rl> *twy, cudaStream_t s);
+                         const TW<Rl> *twy, cudaStream_t s, int64_t sx = 0);
 // loop control ctl (4 ints on the device): [0] update index, [1] any field
 // active after the current update, [2] its value at the last advance
 cudaError_t ns_begin(void *fs, int64_t batch, int *ctl, cudaStream_t s);

@@ -56,12 +56,12 @@ __global__ void k_ns_advance(int *ctl, int use_graph, cudaGraphConditionalHandle
 
 template <class Rl>
 cudaError_t ns_row_pass(V2<Rl> *c1, V2<Rl> *c2, const void *fs, int64_t nx, int64_t ny, int64_t batch,
-                        const TW<Rl> *twx, cudaStream_t s, bool dealias)
+                        const TW<Rl> *twx, cudaStream_t s, bool dealias, bool half)
 {
     int lgy = 0;
     while ((int64_t(1) << lgy) < ny) ++lgy;  // ny is a power of two
-    return launch_row<Rl>(nx, NsRow<Rl>{c1, c2, static_cast<const NsField *>(fs), lgy, dealias ? 1 : 0}, twx,
-                          batch * ny, s);
+    return launch_row<Rl>(nx, NsRow<Rl>{c1, c2, static_cast<const NsField *>(fs), lgy, dealias ? 1 : 0, half ? 1 : 0},
+                          twx, batch * ny, s);
 }
 
 template <class Rl>
@@ -69,21 +69,25 @@ cudaError_t ns_col_pass(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, 
                         const Rl *kxo, const Rl *kyo, const Rl *kx2, const Rl *ky2, const Rl *keepx,
                         const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch,
                         const int *ctl, int midpoint, const TW<Rl> *twy, int *groups_out, cudaStream_t s,
-                        bool dealias)
+                        bool dealias, int64_t sx)
 {
+    if (sx > 0)
+        return ns_col_half<Rl>(c1, c2, w, jn, fs, partials, kxo, kyo, kx2, ky2, keepx, keepy, dt, nu, nx, sx, ny,
+                               batch, ctl, midpoint, twy, groups_out, s, dealias);
     return midpoint ? ns_col_mid<Rl>(c1, c2, w, jn, fs, partials, kxo, kyo, kx2, ky2, keepx, keepy, dt, nu, nx, ny,
                                      batch, ctl, twy, groups_out, s, dealias)
-                    : ns_col_run<Rl, false>(c1, c2, w, jn, fs, partials, kxo, kyo, kx2, ky2, keepx, keepy, dt, nu,
-                                            nx, ny, batch, ctl, twy, groups_out, s, dealias);
+                    : ns_col_run<Rl, false, false>(c1, c2, w, jn, fs, partials, kxo, kyo, kx2, ky2, keepx, keepy, dt,
+                                                   nu, nx, nx, ny, batch, ctl, twy, groups_out, s, dealias);
 }
 
 template <class Rl>
 cudaError_t ns_prep_pass(V2<Rl> *const w[3], const void *fs, V2<Rl> *c1, V2<Rl> *c2, const Rl *kxo, const Rl *kyo,
                          const Rl *kx2, const Rl *ky2, int64_t nx, int64_t ny, int64_t batch,
-                         const TW<Rl> *twy, cudaStream_t s)
+                         const TW<Rl> *twy, cudaStream_t s, int64_t sx)
 {
+    if (sx > 0) return ns_prep_half<Rl>(w, fs, c1, c2, kxo, kyo, kx2, ky2, nx, sx, ny, batch, twy, s);
     NsPrep<Rl> op{w[0], w[1], w[2], static_cast<const NsField *>(fs), c1, c2, kxo, kyo, kx2, ky2,
-                  Rl(1.0 / (double(nx) * double(ny))), nx};
+                  Rl(1.0 / (double(nx) * double(ny))), nx, nx};
     return launch_col<Rl>(ny, nx, op, twy, batch, s);
 }
 
@@ -111,15 +115,16 @@ size_t ns_field_bytes() { return sizeof(NsField); }
 
 #define PSS_INST(Rl)                                                                                         \
     template cudaError_t ns_row_pass<Rl>(V2<Rl> *, V2<Rl> *, const void *, int64_t, int64_t, int64_t,       \
-                                         const TW<Rl> *, cudaStream_t, bool);                                \
+                                         const TW<Rl> *, cudaStream_t, bool, bool);                          \
     template cudaError_t ns_col_pass<Rl>(V2<Rl> *, V2<Rl> *, V2<Rl> *const[3], V2<Rl> *, void *, double *,  \
                                          const Rl *, const Rl *, const Rl *, const Rl *, const Rl *,         \
                                          const Rl *, double, double, int64_t, int64_t, int64_t,             \
-                                         const int *, int, const TW<Rl> *, int *, cudaStream_t, bool);      \
+                                         const int *, int, const TW<Rl> *, int *, cudaStream_t, bool,       \
+                                         int64_t);                                                           \
     template cudaError_t ns_prep_pass<Rl>(V2<Rl> *const[3], const void *, V2<Rl> *, V2<Rl> *, const Rl *,     \
                                           const Rl *,                                                         \
                                           const Rl *, const Rl *, int64_t, int64_t, int64_t, const TW<Rl> *, \
-                                          cudaStream_t);
+                                          cudaStream_t, int64_t);
 PSS_INST(float)
 PSS_INST(double)
 

@@ -91,6 +91,7 @@ template <class Rl> struct NsRow {
     int lgy;      // log2 ny: row r belongs to field r >> lgy
     int dealias;  // 2/3 rule: columns with 3 |mx| >= nx are not written (they stay
                   // zero: the column pass skips them and the mask discards J there)
+    int half;     // half spectra: only columns 0 .. nx/2 of J are read, so only they are written
     __device__ const V2<Rl> *in(int k) const { return k == 0 ? c1 : c2; }
     template <int N, int P, bool BLOCK, class Sm>
     __device__ __forceinline__ void row(V2<Rl> (&v)[2][P], int64_t r, bool ok, int t, const Sm (&sm)[2],
@@ -110,16 +111,24 @@ template <class Rl> struct NsRow {
 #pragma unroll
         for (int m = 0; m < P; ++m, p += T) {
             const int x = t + T * m;
-            const bool kept = !dealias || 3 * (x < N / 2 ? x : N - x) < N;
+            const bool kept = (!dealias || 3 * (x < N / 2 ? x : N - x) < N) && (!half || x <= N / 2);
             if (live && kept) *p = v[0][m];
         }
     }
 };
 
-template <class Rl, bool MID> struct NsCol {
+// Column pass of one fixed-point update.  HALF: the vorticity iterates and
+// J_hat^n are half spectra (columns kx = 0 .. nxf/2 of rows of stride nx),
+// J and C1, C2 stay full-width rows (stride nxf = in_stride); each visited
+// column kx writes the derivative fields at kx and at nxf - kx (the
+// transforms of a real field at -kx are the conjugates of those at kx, with
+// the spectrum taken at -kx), so four inverse transforms per column replace
+// two on twice as many columns.
+template <class Rl, bool MID, bool HALF = false> struct NsCol {
     static constexpr int NIN = 1;
     static constexpr bool LEAN = NS_LEAN;
     static constexpr int PMAX = NS_PMAX;
+    static constexpr int NOUT = HALF ? 4 : 2;  // inverse transforms per column
     __host__ __device__ static constexpr int pmax(int n) { return ns_pmax(n); }
     V2<Rl> *c1, *c2;        // in: J row transforms (c1); out: C1, C2 of w^{k+1}
     V2<Rl> *w0, *w1, *w2;   // vorticity buffers
@@ -128,9 +137,10 @@ template <class Rl, bool MID> struct NsCol {
     double *partials;       // [field][column group]
     const Rl *kxo, *kyo, *kx2, *ky2, *keepx, *keepy;
     Rl half_dt, half_dt_nu, inv_n2;
-    int64_t nx;
+    int64_t nx;             // row stride of w and J_hat^n (half spectra: nxf/2 + 8)
     const int *kptr;  // fixed-point update index of this pass (device, set by k_ns_advance)
     int W;
+    int64_t in_stride;      // row stride of J, C1, C2 (= nxf)
     // 2/3 rule: column groups skip_lo .. skip_lo + skip_n - 1 hold only modes
     // with 3|mx| >= nx, which the mask keeps at zero in w, J and the
     // derivative fields; the pass does not visit them (0, 0 without dealiasing)
@@ -153,18 +163,23 @@ template <class Rl, bool MID> struct NsCol {
         V2<Rl>(&v)[P] = vv[0];
         const int k = *kptr;
         const NsField f = fs[field];
-        const bool live = f.active != 0;
+        const int64_t nxf = in_stride;
+        // half spectra: the padding columns beyond nxf/2 carry nothing
+        const bool valid = !HALF || 2 * int64_t(x) <= nxf;
+        const bool live = f.active != 0 && valid;
         const int64_t base = field * N * nx + x;
         const V2<Rl> *wn = wb(f.idx) + base;
         const V2<Rl> *wk = wb(ns_buf(f.idx, k)) + base;
         V2<Rl> *wk1 = wb(ns_buf(f.idx, k + 1)) + base;
-        const Rl kx = __ldg(kxo + x), kxx = __ldg(kx2 + x), mx = __ldg(keepx + x);
+        const int xs = valid ? x : 0;  // table index (the padding reads column 0's entries)
+        const Rl kx = __ldg(kxo + xs), kxx = __ldg(kx2 + xs), mx = __ldg(keepx + xs);
         double acc = 0.0;
-        // pass 0: J_hat and the update; passes 1, 2: C1 and C2 of the new
-        // iterate (or of the midpoint), inverse transforms through the forward
-        // body; C2 is rebuilt from the iterate this thread has just stored
+        // pass 0: J_hat and the update; passes 1 .. NOUT: the derivative fields
+        // of the new iterate (or of the midpoint), inverse transforms through
+        // the forward body; each later one is rebuilt from the iterate this
+        // thread has just stored
 #pragma unroll 1
-        for (int pass = 0; pass < 3; ++pass) {
+        for (int pass = 0; pass <= NOUT; ++pass) {
             if (pass > 0) conj_all(v);
             block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw);
             if (pass == 0) {
@@ -195,21 +210,35 @@ template <class Rl, bool MID> struct NsCol {
                                      (Rl(2) * a * a_n.y + half_dt * (jk.y + jnv.y)) * inv};
                     const V2<Rl> w1v{a_n.x - inc.x, a_n.y - inc.y};
                     const double ex = double(w1v.x) - double(a_k.x), ey = double(w1v.y) - double(a_k.y);
-                    acc += ex * ex + ey * ey;
+                    if (valid) acc += ex * ex + ey * ey;
                     if (live) wk1[o] = w1v;
                     v[m] = ns_deriv(0, jfield(w1v, a_n), kx, __ldg(kyo + y), kk, inv_n2);
                 }
             } else {
-                conj_all(v);
-                store_line<P, T>(v, (pass == 1 ? c1 : c2) + base, nx, t, live);
-                if (pass == 1) {
+                // output pass - 1: C1 or C2, at kx or (half spectra) mirrored at nxf - kx
+                const int out = pass - 1;
+                const int which = HALF ? out >> 1 : out;
+                const bool mirror = HALF && (out & 1);
+                if (!mirror) conj_all(v);  // the mirrored column stores the conjugate
+                const bool dup = mirror && (x == 0 || 2 * int64_t(x) == nxf);
+                V2<Rl> *dst = (which == 0 ? c1 : c2) + field * N * nxf + (mirror ? nxf - x : x);
+                store_line<P, T>(v, dst, nxf, t, live && !dup);
+                if (pass < NOUT) {
+                    const int nwhich = HALF ? pass >> 1 : pass;
+                    const bool nmirror = HALF && (pass & 1);
+                    const Rl sx = nmirror ? -kx : kx;
+                    // at -kx a field's transform is conj(IFFT(conj(d(-kx, -ky)) w_hat(kx, ky))):
+                    // d(-kx, ky) itself for C1, its negative for C2 = i (kx + i ky) w_hat
+                    const Rl sg = (nmirror && nwhich == 1) ? Rl(-1) : Rl(1);
 #pragma unroll
                     for (int m = 0; m < P; ++m) {
                         const int y = t + T * m;
                         const int64_t o = int64_t(y) * nx;
-                        const V2<Rl> w1v = wk1[o];  // stored by this thread in pass 0
+                        const V2<Rl> w1v = live ? wk1[o] : V2<Rl>{0, 0};  // stored by this thread in pass 0
                         const V2<Rl> a_n = (MID && live) ? wn[o] : V2<Rl>{0, 0};
-                        v[m] = ns_deriv(1, jfield(w1v, a_n), kx, __ldg(kyo + y), kxx + __ldg(ky2 + y), inv_n2);
+                        const V2<Rl> d = ns_deriv(nwhich, jfield(w1v, a_n), sx, __ldg(kyo + y), kxx + __ldg(ky2 + y),
+                                                  inv_n2);
+                        v[m] = V2<Rl>{sg * d.x, sg * d.y};
                     }
                 }
             }
@@ -240,17 +269,19 @@ template <class Rl, bool MID> struct NsCol {
 // w^n in buffer 0: fs == nullptr), and, for the midpoint scheme, at the start
 // of every step (w^n in buffer fs[field].idx), since its last column pass
 // leaves the derivatives of the midpoint rather than those of w^{n+1}
-template <class Rl> struct NsPrep {
+template <class Rl, bool HALF = false> struct NsPrep {
     static constexpr int NIN = 1;
     static constexpr bool LEAN = NS_LEAN;
     static constexpr int PMAX = NS_PMAX;
+    static constexpr int NOUT = HALF ? 4 : 2;
     __host__ __device__ static constexpr int pmax(int n) { return n < 1024 ? NS_PMAX : NS_PREP_PMAX_BIG; }
     const V2<Rl> *w0, *w1, *w2;
     const NsField *fs;
     V2<Rl> *c1, *c2;
     const Rl *kxo, *kyo, *kx2, *ky2;
     Rl inv_n2;
-    int64_t nx;
+    int64_t nx;   // row stride of w (half spectra: nxf/2 + 8)
+    int64_t nxf;  // row stride of C1, C2
     __device__ const V2<Rl> *in(int, int64_t field) const
     {
         const int b = fs ? fs[field].idx : 0;
@@ -264,36 +295,50 @@ template <class Rl> struct NsPrep {
         V2<Rl>(&v)[P] = vv[0];
         const int64_t base = field * N * nx + x;
         const V2<Rl> *w = in(0, field) + base;
-        const Rl kx = __ldg(kxo + x), kxx = __ldg(kx2 + x);
-        // C1 from the staged column, then C2 from the column re-read
+        const bool valid = !HALF || 2 * int64_t(x) <= nxf;
+        const int xs = valid ? x : 0;
+        const Rl kx = __ldg(kxo + xs), kxx = __ldg(kx2 + xs);
+        // the first output from the staged column, the others from the column
+        // re-read; half spectra: C1, C2 at kx and mirrored at nxf - kx
 #pragma unroll 1
-        for (int which = 0; which < 2; ++which) {
-            if (which == 1)
+        for (int out = 0; out < NOUT; ++out) {
+            const int which = HALF ? out >> 1 : out;
+            const bool mirror = HALF && (out & 1);
+            if (out > 0)
 #pragma unroll
                 for (int m = 0; m < P; ++m) v[m] = w[int64_t(t + T * m) * nx];
+            const Rl sx = mirror ? -kx : kx;
+            const Rl sg = (mirror && which == 1) ? Rl(-1) : Rl(1);  // as in NsCol
 #pragma unroll
             for (int m = 0; m < P; ++m) {
                 const int y = t + T * m;
-                v[m] = ns_deriv(which, v[m], kx, __ldg(kyo + y), kxx + __ldg(ky2 + y), inv_n2);
+                const V2<Rl> d = ns_deriv(which, v[m], sx, __ldg(kyo + y), kxx + __ldg(ky2 + y), inv_n2);
+                v[m] = V2<Rl>{sg * d.x, sg * d.y};
             }
             conj_all(v);
             block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw);
-            conj_all(v);
-            store_line<P, T>(v, (which == 0 ? c1 : c2) + base, nx, t, true);
+            if (!mirror) conj_all(v);
+            const bool dup = mirror && (x == 0 || 2 * int64_t(x) == nxf);
+            V2<Rl> *dst = (which == 0 ? c1 : c2) + field * N * nxf + (mirror ? nxf - x : x);
+            store_line<P, T>(v, dst, nxf, t, valid && !dup);
         }
     }
 };
 
-// column pass of one fixed-point update (scheme chosen by MID)
-// the run of column groups (w columns each) whose every column has
-// 3 |mx| >= nx: storage columns x with mx = x (x < nx/2) or x - nx
-inline void ns_masked_groups(int64_t nx, int w, int64_t *lo, int64_t *n)
+// Column groups (w columns each, of a row of stride sx) the column pass
+// skips, as one run [lo, lo + n): with full spectra the groups whose every
+// column has 3 |mx| >= nxf (dealiasing only); with half spectra the groups
+// whose columns all have 2x > nxf (padding) or, dealiasing, 3x >= nxf.
+inline void ns_skip_groups(int64_t nxf, int64_t sx, int w, bool half, bool dealias, int64_t *lo, int64_t *n)
 {
-    auto masked = [nx](int64_t x) { return 3 * (x < nx / 2 ? x : nx - x) >= nx; };
+    auto skipped = [&](int64_t x) {
+        if (half) return 2 * x > nxf || (dealias && 3 * x >= nxf);
+        return dealias && 3 * (x < nxf / 2 ? x : nxf - x) >= nxf;
+    };
     int64_t first = -1, last = -1;
-    for (int64_t g = 0; g < nx / w; ++g) {
+    for (int64_t g = 0; g < sx / w; ++g) {
         bool all = true;
-        for (int64_t x = g * w; x < (g + 1) * w; ++x) all = all && masked(x);
+        for (int64_t x = g * w; x < (g + 1) * w; ++x) all = all && skipped(x);
         if (all) {
             if (first < 0) first = g;
             last = g;
@@ -303,33 +348,48 @@ inline void ns_masked_groups(int64_t nx, int w, int64_t *lo, int64_t *n)
     *n = first < 0 ? 0 : last - first + 1;
 }
 
-template <class Rl, bool MID>
+// column pass of one fixed-point update (scheme chosen by MID, layout by
+// HALF); nxf is the grid's row length, sx the row stride of w and J_hat^n
+template <class Rl, bool MID, bool HALF>
 cudaError_t ns_col_run(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, void *fs, double *partials,
                         const Rl *kxo, const Rl *kyo, const Rl *kx2, const Rl *ky2, const Rl *keepx,
-                        const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch,
+                        const Rl *keepy, double dt, double nu, int64_t nxf, int64_t sx, int64_t ny, int64_t batch,
                         const int *ctl, const TW<Rl> *twy, int *groups_out, cudaStream_t s, bool dealias)
 {
-    NsCol<Rl, MID> op{c1, c2, w[0], w[1], w[2], jn, static_cast<NsField *>(fs), partials, kxo, kyo, kx2, ky2,
-                 keepx, keepy, Rl(0.5 * dt), Rl(0.5 * dt * nu), Rl(1.0 / (double(nx) * double(ny))), nx, ctl, 0,
-                 0, 0};
+    using Op = NsCol<Rl, MID, HALF>;
+    Op op{c1, c2, w[0], w[1], w[2], jn, static_cast<NsField *>(fs), partials, kxo, kyo, kx2, ky2,
+          keepx, keepy, Rl(0.5 * dt), Rl(0.5 * dt * nu), Rl(1.0 / (double(nxf) * double(ny))), sx, ctl, 0,
+          nxf, 0, 0};
     switch (ny) {
-#define PSS_CASE(N)                                                                   \
-    case N:                                                                           \
-        op.W = ColCfgOf<Rl, N, NsCol<Rl, MID>>::W;                                    \
-        if (dealias) ns_masked_groups(nx, op.W, &op.skip_lo, &op.skip_n);             \
-        *groups_out = int(nx / op.W - op.skip_n);                                     \
-        return launch_col_n<Rl, N>(op, twy, nx, batch, s);
+#define PSS_CASE(N)                                                                          \
+    case N:                                                                                  \
+        op.W = ColCfgOf<Rl, N, Op>::W;                                                       \
+        if (sx % op.W) return cudaErrorInvalidValue;                                         \
+        ns_skip_groups(nxf, sx, op.W, HALF, dealias, &op.skip_lo, &op.skip_n);               \
+        *groups_out = int(sx / op.W - op.skip_n);                                            \
+        return launch_col_n<Rl, N>(op, twy, sx, batch, s);
         PSS_FOR_EACH_N(PSS_CASE)
 #undef PSS_CASE
     default: return cudaErrorInvalidValue;
     }
 }
 
-// the midpoint instantiations live in their own translation unit
+// the other instantiations live in their own translation units: midpoint on
+// full spectra (k_ns_mid.cu), both schemes on half spectra (k_ns_half.cu)
 template <class Rl>
 cudaError_t ns_col_mid(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, void *fs, double *partials,
                        const Rl *kxo, const Rl *kyo, const Rl *kx2, const Rl *ky2, const Rl *keepx,
                        const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch,
                        const int *ctl, const TW<Rl> *twy, int *groups_out, cudaStream_t s, bool dealias);
+template <class Rl>
+cudaError_t ns_col_half(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, void *fs, double *partials,
+                        const Rl *kxo, const Rl *kyo, const Rl *kx2, const Rl *ky2, const Rl *keepx,
+                        const Rl *keepy, double dt, double nu, int64_t nxf, int64_t sx, int64_t ny, int64_t batch,
+                        const int *ctl, int midpoint, const TW<Rl> *twy, int *groups_out, cudaStream_t s,
+                        bool dealias);
+template <class Rl>
+cudaError_t ns_prep_half(V2<Rl> *const w[3], const void *fs, V2<Rl> *c1, V2<Rl> *c2, const Rl *kxo, const Rl *kyo,
+                         const Rl *kx2, const Rl *ky2, int64_t nxf, int64_t sx, int64_t ny, int64_t batch,
+                         const TW<Rl> *twy, cudaStream_t s);
 
 }  // namespace pss

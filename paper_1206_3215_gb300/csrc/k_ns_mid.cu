@@ -11,8 +11,8 @@ cudaError_t ns_col_mid(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, v
                        const Rl *keepy, double dt, double nu, int64_t nx, int64_t ny, int64_t batch,
                        const int *ctl, const TW<Rl> *twy, int *groups_out, cudaStream_t s, bool dealias)
 {
-    return ns_col_run<Rl, true>(c1, c2, w, jn, fs, partials, kxo, kyo, kx2, ky2, keepx, keepy, dt, nu, nx, ny, batch,
-                                ctl, twy, groups_out, s, dealias);
+    return ns_col_run<Rl, true, false>(c1, c2, w, jn, fs, partials, kxo, kyo, kx2, ky2, keepx, keepy, dt, nu, nx,
+                                       nx, ny, batch, ctl, twy, groups_out, s, dealias);
 }
 
 #define PSS_INST(Rl)                                                                                          \

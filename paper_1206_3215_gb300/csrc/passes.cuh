@@ -311,6 +311,17 @@ template <class Op> __device__ __forceinline__ auto col_in(const Op &op, int k, 
     else return op.in(k);
 }
 
+// Row stride of a column op's staged inputs: op.in_stride where the op
+// defines it (inputs wider than the columns it visits), else nx.
+template <class Op, class = void> struct HasInStride : std::false_type {};
+template <class Op>
+struct HasInStride<Op, std::void_t<decltype(std::declval<const Op &>().in_stride)>> : std::true_type {};
+template <class Op> __device__ __forceinline__ int64_t in_stride(const Op &op, int64_t nx)
+{
+    if constexpr (HasInStride<Op>::value) return op.in_stride;
+    else return nx;
+}
+
 // Column groups a column op visits: all nx / W of them, or, where the op
 // defines skip_lo / skip_n, all but the skip_n groups from skip_lo on (a
 // contiguous run the op knows to be zero and to stay zero).
@@ -348,7 +359,8 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, VAR>::THREADS, ColCfgOf<Rl
             const int64_t field = tile / groups, x = group_index(op, tile % groups) * C::W + c;
 #pragma unroll
             for (int k = 0; k < NIN; ++k)
-                stage_line<C::P, C::T>(line(b, k), col_in(op, k, field) + field * N * nx + x, nx, t);
+                stage_line<C::P, C::T>(line(b, k), col_in(op, k, field) + field * N * in_stride(op, nx) + x,
+                                       in_stride(op, nx), t);
         }
         cp_async_commit();
     };

@@ -239,3 +239,86 @@ def test_midpoint_graph_direct_and_resume_agree_bitwise(lib, cuda_device, monkey
         g.close()
         h.close()
     assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+# ---------------------------------------------------------------------------
+# Half spectra (rfft = 1): the vorticity iterates and J_hat^n keep kx >= 0
+# only; the derivative fields are written at kx and nx - kx
+
+@pytest.mark.parametrize("scheme", ["cn", "midpoint"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [64, 128])
+def test_half_spectrum_matches_oracle(lib, orc, cuda_device, scheme, precision, n):
+    L, nu, dt, steps = 2 * math.pi, 1e-3, 2.5e-3, 20
+    w0 = S.ns_power_law(n)
+    ref, iters, ok = orc.ns_run(orc.ns_init(w0, True), L, L, nu, dt, steps, scheme=scheme)
+    assert ok
+    g = lib.Grid("ns", n, precision, lx=L, ly=L, dt=dt, nu=nu, tol=1e-10, dealias=1, scheme=scheme, rfft=1)
+    g.set_state(w0[None])
+    g.step(steps)
+    err = rel_l2(g.get_state()[0], orc.ns_field(ref))
+    assert err <= (TOL64 if precision == "fp64" else 1e-5), err
+    if precision == "fp64":
+        assert g.stats()[1] == int(iters.sum())
+    c0, z0, e0 = orc.ns_invariants(ref, L, L)
+    (c, z, e), = g.conserved()
+    assert abs(z - z0) / z0 <= (1e-10 if precision == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_half_spectrum_taylor_green_table4_without_dealiasing(lib, cuda_device, n):
+    # the paper's mode (no 2/3 rule): the Nyquist column is visited and has
+    # no mirror; Table 4's error as with full spectra
+    g0 = _golden("ns_taylor_green_table4.txt")
+    steps, dt, nu = int(g0["steps"]), g0["dt"], g0["nu"]
+    g = lib.Grid("ns", n, "fp64", lx=1.0, ly=1.0, dt=dt, nu=nu, tol=g0["tol"], dealias=0, rfft=1)
+    g.set_state(S.taylor_green_paper(n)[None])
+    g.step(steps)
+    err = np.abs(g.get_state()[0] - S.taylor_green_paper(n, t=steps * dt, nu=nu)).max()
+    assert abs(err - _cn_error(4 * math.pi, 8 * math.pi ** 2, nu, dt, steps)) <= 1e-10
+
+
+def test_half_spectrum_non_square_and_without_dealiasing_matches_oracle(lib, orc, cuda_device):
+    nx, ny, L, nu, dt, steps = 128, 64, 2 * math.pi, 1e-3, 2.5e-3, 10
+    x = S.grid_coords(nx, 0.0, L)
+    y = S.grid_coords(ny, 0.0, L)
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    w0 = np.sin(3 * X) * np.cos(2 * Y) + 0.5 * np.cos(X + Y) + 0.2 * np.sin(5 * X - 3 * Y)
+    for dealias in (1, 0):
+        ref, _, ok = orc.ns_run(orc.ns_init(w0, bool(dealias)), L, L, nu, dt, steps, dealias=bool(dealias))
+        assert ok
+        g = lib.Grid("ns", (nx, ny), "fp64", lx=L, ly=L, dt=dt, nu=nu, dealias=dealias, rfft=1)
+        g.set_state(w0[None])
+        g.step(steps)
+        assert rel_l2(g.get_state()[0], orc.ns_field(ref)) <= TOL64
+
+
+def test_half_spectrum_batch_resume_graphs_and_fields(lib, cuda_device, monkeypatch):
+    # batch = solo, graph = direct launches and checkpoint resume bit for bit;
+    # set_field / get_field of one slot
+    n, L = 64, 2 * math.pi
+    kw = dict(lx=L, ly=L, dt=2.5e-3, nu=1e-3, rfft=1)
+    fields = np.stack([S.taylor_green_2pi(n), S.ns_power_law(n)])
+    res = []
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("PSS_GRAPHS", graphs)
+        g = lib.Grid("ns", n, "fp32", batch=2, **kw)
+        g.set_state(fields)
+        g.step(3)
+        ck = g.checkpoint()
+        g.step(3)
+        together = g.get_state()
+        for i in range(2):
+            h = lib.Grid("ns", n, "fp32", **kw)
+            h.set_state(fields[i:i + 1])
+            h.step(6)
+            assert np.array_equal(h.get_state()[0], together[i])
+            assert np.array_equal(g.get_field(i), together[i])
+        r = lib.Grid("ns", n, "fp32", batch=2, **kw)
+        r.restore(ck)
+        r.step(3)
+        assert np.array_equal(r.get_state(), together)
+        g.set_field(0, fields[1])
+        g.step(2)
+        res.append((g.get_state(), g.stats()))
+    assert np.array_equal(res[0][0], res[1][0]) and res[0][1] == res[1][1]
