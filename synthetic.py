@@ -126,7 +126,7 @@ def serving_mix(count: int, rate_hz: float, sizes=(128, 256, 512, 1024, 2048), s
             params = {"dt": 1e-3, "lx": 10 * math.pi, "ly": 10 * math.pi, "rfft": 1}
         else:
             state = (ns_power_law(n, seed=fseed),)
-            params = {"dt": 2.5e-4, "lx": 2 * math.pi, "ly": 2 * math.pi, "nu": 1e-3}
+            params = {"dt": 2.5e-4, "lx": 2 * math.pi, "ly": 2 * math.pi, "nu": 1e-3, "rfft": 1}
         out.append({"rid": rid, "eq": eq, "n": n, "steps": k, "state": state, "arrival": t,
                     "precision": "fp32", "params": params})
     return out
