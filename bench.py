@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-other", action="store_true", help="skip the SG / NS / 4096^2 NLS lines")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--other-only", action="store_true",
+                    help="run only the other-workload lines (one JSON object), e.g. for a profiler")
+    ap.add_argument("--only", default=None, help="with --other-only: just this line (e.g. sg_2048_fp32_half)")
     ap.add_argument("--paper-tables", action="store_true",
                     help="replay the runs of Tables 2-4 instead (one JSON line with both timings)")
     ap.add_argument("--serve-requests", type=int, default=120)
@@ -255,14 +258,22 @@ def timed_steps(grid, steps: int, stream) -> float:
     return e0.elapsed_time(e1) / steps
 
 
-def other_paths(stream, rank: int):
+def other_paths(stream, rank: int, only=None, autotune: bool = True):
     """Device-timed throughput of the other equations at their workload grids
     (sine-Gordon 2048^2, Navier-Stokes 4096^2 both schemes) and of the NLS step
-    at 4096^2, where one pass moves 256 MiB per field pair."""
+    at 4096^2, where one pass moves 256 MiB per field pair.  `only` restricts
+    the run to one named line."""
     import paper_1206_3215_gb300 as P
     import synthetic as S
     out = {}
     sc = stream.cuda_stream
+
+    def want(name):
+        return only is None or only == name
+
+    def tune(g):
+        if autotune:
+            g.autotune(4)
 
     def rate(points, ms):
         return points / (ms / 1e3) / 1e9
@@ -270,19 +281,24 @@ def other_paths(stream, rank: int):
     # sine-Gordon, Eq. 3: 2048^2, box [-5 pi, 5 pi)^2, dt 1e-3; full complex
     # spectra and half spectra (real-to-complex rows)
     for prec, B, K, rfft in (("fp32", 8, 50, 0), ("fp32", 8, 50, 1), ("fp64", 4, 5, 0), ("fp64", 4, 5, 1)):
+        name = f"sg_2048_{prec}" + ("_half" if rfft else "")
+        if not want(name):
+            continue
         n, Ls = 2048, 10 * math.pi
         u0, v0 = S.sg_gaussian(n, batch=B, seed=S.SEED_BASE + 2 + 100000 * rank)
         g = P.Grid("sg", n, prec, batch=B, lx=Ls, ly=Ls, dt=1e-3, stream=sc, rfft=rfft)
         g.set_state(u0, v0)
-        g.autotune(4)
+        tune(g)
         g.step(3)
         ms = timed_steps(g, K, stream)
-        out[f"sg_2048_{prec}" + ("_half" if rfft else "")] = {"value": rate(B * n * n, ms), "unit": UNIT,
-                                                              "batch": B, "steps": K, "ms_per_step": ms}
+        out[name] = {"value": rate(B * n * n, ms), "unit": UNIT, "batch": B, "steps": K, "ms_per_step": ms}
         g.close()
     # Navier-Stokes 4096^2, [0, 2 pi)^2, nu 1e-3, dt 2.5e-4, tol 1e-10, 2/3 rule;
     # both schemes, full and half spectra
     for scheme, rfft in (("cn", 0), ("midpoint", 0), ("cn", 1), ("midpoint", 1)):
+        name = f"ns_4096_fp32_{scheme}" + ("_half" if rfft else "")
+        if not want(name):
+            continue
         n, Ln = 4096, 2 * math.pi
         g = P.Grid("ns", n, "fp32", lx=Ln, ly=Ln, dt=2.5e-4, nu=1e-3, tol=1e-10, dealias=1, scheme=scheme,
                    rfft=rfft, stream=sc)
@@ -292,16 +308,17 @@ def other_paths(stream, rank: int):
         u0 = g.stats()[1]
         K = 10
         ms = timed_steps(g, K, stream)
-        out[f"ns_4096_fp32_{scheme}" + ("_half" if rfft else "")] = {
-            "value": rate(n * n, ms), "unit": UNIT, "steps": K, "ms_per_step": ms,
-            "jacobians_per_step": (g.stats()[1] - u0) / K}
+        out[name] = {"value": rate(n * n, ms), "unit": UNIT, "steps": K, "ms_per_step": ms,
+                     "jacobians_per_step": (g.stats()[1] - u0) / K}
         g.close()
     # NLS at 4096^2 (2 fields, 256 MiB of state): the row/column pass roofline
+    if not want("nls_4096_fp32"):
+        return out
     n, B, K = 4096, 2, 50
     f = S.nls_gaussian(n, seed=S.SEED_BASE + 1 + 100000 * rank, batch=B).astype("complex64")
     g = P.Grid("nls", n, "fp32", batch=B, lx=L, ly=L, dt=DT, stream=sc)
     g.set_state(f)
-    g.autotune(4)
+    tune(g)
     g.step(3)
     P.pss_set_profiling(g.h, True)
     ms = timed_steps(g, K, stream)
@@ -523,7 +540,7 @@ def run_ours(args):
                  "wall_s": st["wall_s"], "pools": st["pools"], "rounds": st["rounds"],
                  "mix": "NLS/SG/NS FP32, N in {128,256,512,1024,2048}, 50-500 steps, min(8, 2^22/N^2) slots per pool"}
 
-    other = None if args.no_other else other_paths(stream, rank)
+    other = None if args.no_other else other_paths(stream, rank, autotune=not args.no_autotune)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -561,6 +578,12 @@ def main():
     args = parse()
     if args.paper_tables:
         return run_paper_tables(args)
+    if args.other_only:
+        import torch
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        print(json.dumps({"other_paths": other_paths(stream, 0, args.only, not args.no_autotune)}), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -183,6 +183,14 @@ template <class W> __device__ __forceinline__ const W *launder(const W *p)
     return q;
 }
 
+// Ask for the line holding p to be brought into L2 (no register is written):
+// used at the start of a tile for the arrays its update reads later, so those
+// loads wait for L2 rather than for HBM.
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Register fence: every value of v is materialised here and nothing that
 // uses v moves above it, so the two transforms of a fused pass are not
 // interleaved (which would keep both transforms' temporaries live).

@@ -174,6 +174,15 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
         const int xs = valid ? x : 0;  // table index (the padding reads column 0's entries)
         const Rl kx = __ldg(kxo + xs), kxx = __ldg(kx2 + xs), mx = __ldg(keepx + xs);
         double acc = 0.0;
+        if (live) {  // the update reads w^n, w^k (and J_hat^n) after the forward transform
+#pragma unroll
+            for (int m = 0; m < P; ++m) {
+                const int64_t o = int64_t(t + T * m) * nx;
+                prefetch_l2(wn + o);
+                prefetch_l2(wk + o);
+                if (!MID && k > 0) prefetch_l2(jn + base + o);
+            }
+        }
         // pass 0: J_hat and the update; passes 1 .. NOUT: the derivative fields
         // of the new iterate (or of the midpoint), inverse transforms through
         // the forward body; each later one is rebuilt from the iterate this

@@ -80,25 +80,47 @@ template <class Rl> struct SgCol {
         constexpr int T = N / P;
         V2<Rl>(&v)[P] = vv[0];
         const int64_t base = field * N * nx + x;
+        const int64_t step = int64_t(T) * nx;
+        {
+            // u and d are read only after the forward transform: have them in L2 by then
+            const V2<Rl> *qu = u + base + int64_t(t) * nx, *qd = d + base + int64_t(t) * nx;
+#pragma unroll
+            for (int m = 0; m < P; ++m, qu += step, qd += step) {
+                prefetch_l2(qu);
+                prefetch_l2(qd);
+            }
+        }
         auto update = [&]() {
             const Rl kx = __ldg(kx2 + x);
             // one running pointer per array (T rows apart), so the 2P loads and
-            // stores do not each hold a 64-bit address
-            const int64_t step = int64_t(T) * nx;
+            // stores do not each hold a 64-bit address; loads in chunks of CH
+            // points ahead of that chunk's stores (u and d may alias as far as
+            // the compiler knows, so it would not move a load above a store)
+            constexpr int CH = P < 4 ? P : 4;
             V2<Rl> *pu = u + base + int64_t(t) * nx, *pd = d + base + int64_t(t) * nx;
 #pragma unroll
-            for (int m = 0; m < P; ++m) {
-                const int y = t + T * m;
-                const V2<Rl> un = *pu, dn = *pd;
-                const Rl a = dt2 * (kx + __ldg(ky2 + y));
-                const Rl inv = rcp_(Rl(1) + Rl(0.25) * a);
-                const V2<Rl> dn1{dn.x - (a * un.x + dt2 * v[m].x) * inv, dn.y - (a * un.y + dt2 * v[m].y) * inv};
-                const V2<Rl> un1{un.x + dn1.x, un.y + dn1.y};
-                *pd = dn1;
-                *pu = un1;
-                v[m] = cscale(un1, inv_n2);
-                pu += step;
-                pd += step;
+            for (int m0 = 0; m0 < P; m0 += CH) {
+                V2<Rl> un[CH], dn[CH];
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    un[c] = pu[c * step];
+                    dn[c] = pd[c * step];
+                }
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    const int m = m0 + c;
+                    const int y = t + T * m;
+                    const Rl a = dt2 * (kx + __ldg(ky2 + y));
+                    const Rl inv = rcp_(Rl(1) + Rl(0.25) * a);
+                    const V2<Rl> dn1{dn[c].x - (a * un[c].x + dt2 * v[m].x) * inv,
+                                     dn[c].y - (a * un[c].y + dt2 * v[m].y) * inv};
+                    const V2<Rl> un1{un[c].x + dn1.x, un[c].y + dn1.y};
+                    pd[c * step] = dn1;
+                    pu[c * step] = un1;
+                    v[m] = cscale(un1, inv_n2);
+                }
+                pu += CH * step;
+                pd += CH * step;
             }
         };
         if constexpr (sg_shared(sizeof(Rl))) {
