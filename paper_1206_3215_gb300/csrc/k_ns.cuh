@@ -192,10 +192,22 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
             if (pass > 0) conj_all(v);
             block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw);
             if (pass == 0) {
+                // loads of CH points ahead of their stores (the buffers may alias
+                // as far as the compiler knows, so it would not reorder them)
+                constexpr int CH = 4;
+                V2<Rl> ln[CH], lk[CH], lj[CH];
 #pragma unroll
                 for (int m = 0; m < P; ++m) {
                     const int y = t + T * m;
                     const int64_t o = int64_t(y) * nx;
+                    if (m % CH == 0)
+#pragma unroll
+                        for (int c = 0; c < CH && m + c < P; ++c) {
+                            const int64_t oc = int64_t(t + T * (m + c)) * nx;
+                            ln[c] = live ? wn[oc] : V2<Rl>{0, 0};
+                            lk[c] = live ? wk[oc] : V2<Rl>{0, 0};
+                            if (!MID && k > 0) lj[c] = live ? jn[base + oc] : V2<Rl>{0, 0};
+                        }
                     const Rl mask = mx * __ldg(keepy + y);
                     const V2<Rl> jk{v[m].x * mask, v[m].y * mask};
                     // midpoint: jk is already J((w^k + w^n)/2), used twice below
@@ -204,11 +216,11 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
                         if (k == 0) {
                             if (live) jn[base + o] = jk;
                         } else {
-                            jnv = live ? jn[base + o] : jk;
+                            jnv = live ? lj[m % CH] : jk;
                         }
                     }
-                    const V2<Rl> a_n = live ? wn[o] : V2<Rl>{0, 0};
-                    const V2<Rl> a_k = live ? wk[o] : V2<Rl>{0, 0};
+                    const V2<Rl> a_n = ln[m % CH];
+                    const V2<Rl> a_k = lk[m % CH];
                     const Rl kk = kxx + __ldg(ky2 + y);
                     // w^{k+1} = [(1 - a) w^n - dt/2 (J^k + J^n)] / (1 + a), a = dt nu |k|^2 / 2,
                     // formed as w^n minus a small increment so that FP32 rounds
