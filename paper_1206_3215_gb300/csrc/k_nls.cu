@@ -20,10 +20,20 @@ namespace pss {
 //   sin 2a = 2 sin a (1 + (cos a - 1)),  cos 2a - 1 = 2 (cos a - 1)(cos a - 1 + 2),
 // which keeps both terms free of cancellation; k is bounded by the exponent
 // range, so a non-finite phase ends in NaN after a bounded loop.
+template <class Rl> constexpr Rl phase_taylor_range() { return sizeof(Rl) == 4 ? Rl(0.5) : Rl(0.0625); }
+
+// the Taylor sums alone (|a| within phase_taylor_range)
+template <class Rl> __device__ __forceinline__ void phase_taylor(Rl a, Rl &sn, Rl &cm1)
+{
+    const Rl t2 = a * a;
+    sn = a * (Rl(1) + t2 * (Rl(-1.0 / 6) + t2 * (Rl(1.0 / 120) + t2 * (Rl(-1.0 / 5040) + t2 * Rl(1.0 / 362880)))));
+    cm1 = t2 * (Rl(-0.5) + t2 * (Rl(1.0 / 24) + t2 * (Rl(-1.0 / 720) + t2 * (Rl(1.0 / 40320) + t2 * Rl(-1.0 / 3628800)))));
+}
+
 template <class Rl> __device__ __forceinline__ void phase_terms(Rl th, Rl &sn, Rl &cm1)
 {
     constexpr int KMAX = sizeof(Rl) == 4 ? 130 : 1026;
-    constexpr Rl A = sizeof(Rl) == 4 ? Rl(0.5) : Rl(0.0625);
+    constexpr Rl A = phase_taylor_range<Rl>();
     Rl a = th;
     int k = 0;
 #pragma unroll 1
@@ -31,9 +41,7 @@ template <class Rl> __device__ __forceinline__ void phase_terms(Rl th, Rl &sn, R
         a *= Rl(0.5);
         ++k;
     }
-    const Rl t2 = a * a;
-    sn = a * (Rl(1) + t2 * (Rl(-1.0 / 6) + t2 * (Rl(1.0 / 120) + t2 * (Rl(-1.0 / 5040) + t2 * Rl(1.0 / 362880)))));
-    cm1 = t2 * (Rl(-0.5) + t2 * (Rl(1.0 / 24) + t2 * (Rl(-1.0 / 720) + t2 * (Rl(1.0 / 40320) + t2 * Rl(-1.0 / 3628800)))));
+    phase_taylor(a, sn, cm1);
 #pragma unroll 1
     for (; k > 0; --k) {
         const Rl s2 = Rl(2) * sn * (Rl(1) + cm1);
@@ -64,16 +72,32 @@ template <class Rl> struct NlsRow {
         const Sm &sm = smm[0];
         V2<Rl> *p = data + row * N;
         auto nonlinear = [&]() {
+            // psi exp(-i th) = psi + psi (cos th - 1 - i sin th): the
+            // increment is formed without cancellation, so the modulus is
+            // kept to the final rounding.  When every phase of this thread is
+            // in the Taylor range (always, at the workload's dt |psi|^2), the
+            // straight-line Taylor code runs; the halving path is out of line.
+            Rl big = Rl(0);
 #pragma unroll
-            for (int m = 0; m < P; ++m) {
-                // psi exp(-i th) = psi + psi (cos th - 1 - i sin th): the
-                // increment is formed without cancellation, so the modulus is
-                // kept to the final rounding
-                const Rl x = v[m].x, y = v[m].y;
-                Rl sn, cm1;
-                phase_terms(sigma_dt * (x * x + y * y), sn, cm1);
-                v[m].x = x + (x * cm1 + y * sn);
-                v[m].y = y + (y * cm1 - x * sn);
+            for (int m = 0; m < P; ++m) big = fmax(big, fabs(sigma_dt * (v[m].x * v[m].x + v[m].y * v[m].y)));
+            if (big <= phase_taylor_range<Rl>()) {
+#pragma unroll
+                for (int m = 0; m < P; ++m) {
+                    const Rl x = v[m].x, y = v[m].y;
+                    Rl sn, cm1;
+                    phase_taylor(sigma_dt * (x * x + y * y), sn, cm1);
+                    v[m].x = x + (x * cm1 + y * sn);
+                    v[m].y = y + (y * cm1 - x * sn);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < P; ++m) {
+                    const Rl x = v[m].x, y = v[m].y;
+                    Rl sn, cm1;
+                    phase_terms(sigma_dt * (x * x + y * y), sn, cm1);
+                    v[m].x = x + (x * cm1 + y * sn);
+                    v[m].y = y + (y * cm1 - x * sn);
+                }
             }
         };
         if constexpr (PSS_SHARED_FFT && sizeof(Rl) == 4) {
