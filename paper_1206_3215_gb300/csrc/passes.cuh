@@ -64,6 +64,9 @@ namespace pss {
 #ifndef PSS_COL_WIDE_THREADS
 #define PSS_COL_WIDE_THREADS 512
 #endif
+#ifndef PSS_COL_WMAX
+#define PSS_COL_WMAX 8
+#endif
 // FP32 (measured, 1024^2): one shared-memory buffer per CTA and two CTAs per
 // SM (<= 128 registers) beat a double-buffered CTA alone by 9 %; FP64 keeps
 // the double buffer and one CTA per SM.
@@ -102,7 +105,7 @@ template <class Rl> struct Shape {
     // where 32-byte segments fit in 256 threads, the wider tile was slower)
     __host__ __device__ static constexpr int cols_capped(int n, int p, int nbuf, int cap)
     {
-        int w = sizeof(Rl) == 4 ? 8 : 4;
+        int w = sizeof(Rl) == 4 ? PSS_COL_WMAX : 4;
         while (w > 1 && ((long)nbuf * w * (n + n / 16) * ESZ > 200 * 1024L || w * (n / p) > cap)) w /= 2;
         return w;
     }
