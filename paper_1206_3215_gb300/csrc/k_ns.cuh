@@ -52,6 +52,11 @@ __host__ __device__ constexpr int ns_pmax(int n) { return n <= 1024 ? NS_PMAX : 
 #define NS_LEAN true
 #endif
 
+// correctly rounded reciprocal (the value 1 / x rounds to, without the
+// division's instruction sequence)
+__device__ __forceinline__ float ns_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double ns_rcp(double x) { return __drcp_rn(x); }
+
 struct NsField {
     int idx;        // buffer holding w^n
     int active;     // still iterating in this step
@@ -226,7 +231,7 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
                     // formed as w^n minus a small increment so that FP32 rounds
                     // the increment, not the nearly-unit decay factor, every step
                     const Rl a = half_dt_nu * kk;
-                    const Rl inv = Rl(1) / (Rl(1) + a);
+                    const Rl inv = ns_rcp(Rl(1) + a);  // correctly rounded, as 1 / (1 + a)
                     const V2<Rl> inc{(Rl(2) * a * a_n.x + half_dt * (jk.x + jnv.x)) * inv,
                                      (Rl(2) * a * a_n.y + half_dt * (jk.y + jnv.y)) * inv};
                     const V2<Rl> w1v{a_n.x - inc.x, a_n.y - inc.y};
