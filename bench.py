@@ -10,8 +10,9 @@ step of every field of the batch.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle (the only reference this build
-has) on the host cores, on a bounded sample of the same workload.
+--impl reference times the FP64 CPU oracle (the program has no other
+reference implementation) on the host cores, on a bounded sample of the same
+workload.
 Prints one JSON line (rank 0).
 """
 from __future__ import annotations
