@@ -177,6 +177,7 @@ int pss_grid::sync()
 {
     int rc = cuda(cudaStreamSynchronize(stream), "stream sync");
     if (rc) return rc;
+    if ((rc = check_pass_status())) return rc;
     if ((rc = check_ns_nonconv())) return rc;
     if (nonconv_pending) {
         nonconv_pending = false;
@@ -254,6 +255,21 @@ int pss_grid::ns_update_count(int64_t *n)
 }
 
 // Report (and clear) fields that reached max_iter since the last check.
+// a pass kernel that gave up waiting for a tile copy left its tiles
+// unfinished: the state is no longer valid
+int pss_grid::check_pass_status()
+{
+    int *dev_slot = reinterpret_cast<int *>(flags) + pss::FLAG_SLOT_PASS_STATUS;
+    int *host_slot = reinterpret_cast<int *>(host_flags) + pss::FLAG_SLOT_PASS_STATUS;
+    int rc = cuda(cudaMemcpyAsync(host_slot, dev_slot, sizeof(int), cudaMemcpyDeviceToHost, stream), "status copy");
+    if (rc || (rc = cuda(cudaStreamSynchronize(stream), "sync"))) return rc;
+    if (*host_slot == 0) return PSS_OK;
+    *host_slot = 0;
+    if ((rc = cuda(cudaMemsetAsync(dev_slot, 0, sizeof(int), stream), "status reset"))) return rc;
+    has_state = false;
+    return fail(PSS_E_CUDA, "a column-pass tile copy did not arrive in time; the state is lost (set it again)");
+}
+
 int pss_grid::check_ns_nonconv()
 {
     if (p.eq != PSS_EQ_NS || !has_state) return PSS_OK;
@@ -296,7 +312,8 @@ template <class Rl> int nls_step(pss_grid *g, int64_t n)
     const Rl sdt = Rl(g->p.sigma * g->p.dt);
     auto col = [&](int full, Rl scale) {
         return nls_col_pass<Rl>(B<Rl>(g, 0), g->nx, g->ny, g->batch, scale, Tw<Rl>(g->ax[full]),
-                                Tw<Rl>(g->by[full]), Tw<Rl>(g->twy), g->stream);
+                                Tw<Rl>(g->by[full]), Tw<Rl>(g->twy),
+                                reinterpret_cast<int *>(g->flags) + FLAG_SLOT_PASS_STATUS, g->stream);
     };
     if (n == 0) return PSS_OK;
     int rc;

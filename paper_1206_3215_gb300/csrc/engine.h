@@ -118,6 +118,7 @@ struct pss_grid {
         drop_graphs();
     }
     int check_ns_nonconv();
+    int check_pass_status();
 
     size_t field_bytes() const { return size_t(ntot) * esz; }
     double dA() const { return (p.lx / double(nx)) * (p.ly / double(ny)); }

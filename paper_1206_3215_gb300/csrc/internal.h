@@ -36,10 +36,11 @@ cudaError_t nls_row_pass(V2<Rl> *data, int64_t nx, int64_t rows_total, Rl sigma_
                          const TW<Rl> *twx, cudaStream_t s);
 // Column pass: column forward FFT, multiply by scale * a[x] * b[y]
 // (a = exp(-i kx^2 tau), b = exp(-i ky^2 tau); the tables hold a - 1 and
-// b - 1, stored like twiddles), column inverse FFT.
+// b - 1, stored like twiddles), column inverse FFT.  *status gets
+// STATUS_TMA_TIMEOUT if a tile copy never arrived (the pass is then incomplete).
 template <class Rl>
 cudaError_t nls_col_pass(V2<Rl> *data, int64_t nx, int64_t ny, int64_t batch, Rl scale,
-                         const TW<Rl> *ax, const TW<Rl> *by, const TW<Rl> *twy, cudaStream_t s);
+                         const TW<Rl> *ax, const TW<Rl> *by, const TW<Rl> *twy, int *status, cudaStream_t s);
 
 // ---- sine-Gordon passes (k_sg.cu) ---------------------------------------------
 // Row pass on H (column inverse transform of uhat^n / (nx ny)): row inverse
@@ -129,5 +130,9 @@ cudaError_t ns_sums(const void *fs, V2<Rl> *const w[3], int64_t nx, int64_t ny, 
 // status bits written by reductions
 constexpr unsigned FLAG_NONFINITE = 1u;
 constexpr unsigned FLAG_NOT_CONVERGED = 2u;
+
+// int slot of the grid's 64-byte device flag block that pass kernels report
+// a lost tile copy in (slots 0 .. 3 carry the NS step control)
+constexpr int FLAG_SLOT_PASS_STATUS = 8;
 
 }  // namespace pss

@@ -140,7 +140,8 @@ template <class Rl> struct NlsCol {
     int64_t nx;
     Rl scale;
     const TW<Rl> *ax, *by;  // exp(-i kx^2 tau) - 1, exp(-i ky^2 tau) - 1
-    __device__ const V2<Rl> *in(int) const { return data; }
+    int *status;            // set when a tile copy did not arrive
+    __host__ __device__ const V2<Rl> *in(int) const { return data; }
     template <int N, int P, bool BLOCK, class Sm>
     __device__ __forceinline__ void col(V2<Rl> (&vv)[1][P], int64_t field, int x, int t,
                                         const Sm (&smm)[1], const TW<Rl> *tw) const
@@ -189,16 +190,16 @@ cudaError_t nls_row_pass(V2<Rl> *data, int64_t nx, int64_t rows_total, Rl sigma_
 
 template <class Rl>
 cudaError_t nls_col_pass(V2<Rl> *data, int64_t nx, int64_t ny, int64_t batch, Rl scale,
-                         const TW<Rl> *ax, const TW<Rl> *by, const TW<Rl> *twy, cudaStream_t s)
+                         const TW<Rl> *ax, const TW<Rl> *by, const TW<Rl> *twy, int *status, cudaStream_t s)
 {
-    return launch_col<Rl>(ny, nx, NlsCol<Rl>{data, nx, scale, ax, by}, twy, batch, s);
+    return launch_col<Rl>(ny, nx, NlsCol<Rl>{data, nx, scale, ax, by, status}, twy, batch, s);
 }
 
 #define PSS_INST(Rl)                                                                            \
     template cudaError_t nls_row_pass<Rl>(V2<Rl> *, int64_t, int64_t, Rl, const TW<Rl> *,        \
                                           cudaStream_t);                                          \
     template cudaError_t nls_col_pass<Rl>(V2<Rl> *, int64_t, int64_t, int64_t, Rl,               \
-                                          const TW<Rl> *, const TW<Rl> *, const TW<Rl> *,        \
+                                          const TW<Rl> *, const TW<Rl> *, const TW<Rl> *, int *, \
                                           cudaStream_t);
 PSS_INST(float)
 PSS_INST(double)

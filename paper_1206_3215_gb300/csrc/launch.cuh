@@ -110,6 +110,43 @@ inline cudaError_t launch_col_v(Op op, const TW<Rl> *tw, int64_t nx, int64_t bat
     return cudaGetLastError();
 }
 
+// PSS_TMA=0 stages column tiles with per-point cp.async copies instead of
+// tensor copies (read per launch)
+inline bool tma_enabled()
+{
+    const char *e = getenv("PSS_TMA");
+    return !(e && e[0] == '0' && e[1] == 0);
+}
+
+template <class Rl, int N, class Op> constexpr bool tma_col()
+{
+    using C = ColCfgOf<Rl, N, Op, 0>;
+    return TmaCol<Op>::value && sizeof(Rl) == 4 && C::BLOCK && C::NBUF == 1 && N >= 256 && N <= 1024 &&
+           (C::W * sizeof(V2<Rl>)) % 16 == 0;
+}
+
+template <class Rl, int N, class Op>
+inline cudaError_t launch_col_tma(Op op, const TW<Rl> *tw, int64_t nx, int64_t batch, cudaStream_t s)
+{
+    using C = ColCfgOf<Rl, N, Op, 0>;
+    auto k = k_col_tma<Rl, N, Op>;
+    constexpr size_t smem = tma_col_smem<C>();
+    static std::atomic<unsigned> done{0};
+    static int ctas[32] = {};
+    cudaError_t e = allow_smem(k, smem, done);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (nx / C::W) * batch;
+    if (tiles <= 0) return cudaSuccess;
+    if (tiles > INT32_MAX - 2 * 65536) return cudaErrorInvalidValue;  // the kernel counts tiles in 32 bits
+    CUtensorMap map;
+    if ((e = encode_col_map(&map, op.in(0), int(sizeof(V2<Rl>)), nx, N, batch, C::W)) != cudaSuccess) return e;
+    int grid = 0;
+    if ((e = resident_ctas(k, C::THREADS, smem, ctas, &grid)) != cudaSuccess) return e;
+    if (tiles < grid) grid = int(tiles);
+    k<<<dim3(unsigned(grid)), C::THREADS, smem, s>>>(map, op, tw, nx, batch);
+    return cudaGetLastError();
+}
+
 template <class Rl, int N, class Op>
 inline cudaError_t launch_row_n(Op op, const TW<Rl> *tw, int64_t rows_total, cudaStream_t s)
 {
@@ -129,6 +166,8 @@ inline cudaError_t launch_col_n(Op op, const TW<Rl> *tw, int64_t nx, int64_t bat
         if (nx % ColCfgOf<Rl, N, Op, 1>::W == 0 && plan_pick(slot) == 1)
             return launch_col_v<Rl, N, Op, 1>(op, tw, nx, batch, s);
     }
+    if constexpr (tma_col<Rl, N, Op>())
+        if (tma_enabled()) return launch_col_tma<Rl, N, Op>(op, tw, nx, batch, s);
     return launch_col_v<Rl, N, Op, 0>(op, tw, nx, batch, s);
 }
 

@@ -20,6 +20,7 @@
 // one read and one write of every array it touches.
 #pragma once
 #include "fft_core.cuh"
+#include "tma.cuh"
 
 #include <type_traits>
 #include <utility>
@@ -393,6 +394,64 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, VAR>::THREADS, ColCfgOf<Rl
         fft_sync<C::BLOCK>();
     }
     cp_async_wait<0>();
+}
+
+// ----------------------------------------------------------------------------
+// Column pass whose tiles arrive by one tensor copy each (see tma.cuh): for
+// ops with one input array of row stride nx that visit every column group and
+// name a status word (op.status).  The tile lands as a dense [N][W] block at
+// the start of the buffer; thread (c, t) reads its points t + T m of column c
+// from there (a warp reads 32 consecutive points), and the padded column
+// lines of the same buffer then serve as the transforms' exchange space (the
+// first exchange store comes after a CTA barrier, so after every read).
+template <class Op, class = void> struct TmaCol : std::false_type {};
+template <class Op>
+struct TmaCol<Op, std::void_t<decltype(std::declval<const Op &>().status)>>
+    : std::integral_constant<bool, Op::NIN == 1 && !FieldIn<Op>::value && !HasInStride<Op>::value &&
+                                       !SkipsGroups<Op>::value> {};
+
+// dynamic shared memory of the tensor-copy column pass: the buffer, room to
+// align it to 128 bytes and the mbarrier
+template <class C> constexpr size_t tma_col_smem() { return C::SMEM + 128 + 16; }
+
+template <class Rl, int N, class Op>
+__global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, N, Op, 0>::MIN_CTAS)
+    k_col_tma(const __grid_constant__ CUtensorMap map, Op op, const TW<Rl> *__restrict__ tw, int64_t nx,
+              int64_t batch)
+{
+    using C = ColCfgOf<Rl, N, Op, 0>;
+    using V = V2<Rl>;
+    using Sm = SmemLine<V, C::PADLOG>;
+    static_assert(C::NBUF == 1, "one staging buffer");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *const buf = reinterpret_cast<V *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    const unsigned sbar = smem_addr(buf + C::BUF);
+    const int c = threadIdx.x % C::W, t = threadIdx.x / C::W;
+    // 32-bit tile counters (the launcher checks the count): fewer live registers
+    const int groups = int(nx / C::W), tiles = groups * int(batch);
+    if (threadIdx.x == 0) mbar_init(sbar, 1);
+    __syncthreads();
+    unsigned parity = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, parity ^= 1u) {
+        const int field = tile / groups;
+        const int x0 = (tile - field * groups) * C::W;
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();  // the previous tile's shared-memory accesses come first
+            mbar_arrive_expect_tx(sbar, unsigned(N * C::W * sizeof(V)));
+            tma_load_4d(smem_addr(buf), &map, sbar, 2 * x0, 0, 0, field);
+        }
+        const bool landed = mbar_wait(sbar, parity, TMA_WAIT_LIMIT);
+        if (__syncthreads_or(!landed)) {
+            if (threadIdx.x == 0) atomicOr(op.status, STATUS_TMA_TIMEOUT);
+            return;
+        }
+        V v[1][C::P];
+#pragma unroll
+        for (int m = 0; m < C::P; ++m) v[0][m] = buf[(t + C::T * m) * C::W + c];
+        const Sm sm[1] = {Sm{buf + c * C::STRIDE}};
+        op.template col<N, C::P, C::BLOCK>(v, int64_t(field), x0 + c, t, sm, tw);
+        fft_sync<C::BLOCK>();  // every read of this tile is done before the next copy lands
+    }
 }
 
 // ----------------------------------------------------------------------------

@@ -74,3 +74,23 @@ def test_autotune_keeps_state_and_one_plan_per_key(lib, cuda_device, eq):
     alone = alone if isinstance(alone, tuple) else (alone,)
     for a, b in zip(alone, together):
         assert np.array_equal(a[0], b[1])
+
+
+@pytest.mark.parametrize("n", [256, 512, 1024])
+def test_tensor_copy_staging_is_bitwise_equal(lib, cuda_device, monkeypatch, n):
+    # The NLS column pass stages its tiles by one tensor copy each (PSS_TMA
+    # unset) or by per-point copies (PSS_TMA=0): the arithmetic is the same,
+    # so the states agree bit for bit, including a batch whose tiles wrap
+    # from one field to the next
+    p0 = S.nls_gaussian(n, batch=3)
+    out = []
+    for tma in ("1", "0"):
+        monkeypatch.setenv("PSS_TMA", tma)
+        monkeypatch.setenv("PSS_PLAN", "0")
+        g = lib.Grid("nls", n, "fp32", batch=3, lx=L, ly=L, x0=-L / 2, y0=-L / 2, dt=1e-3)
+        g.set_state(p0)
+        g.step(7)
+        g.sync()
+        out.append(g.get_state())
+        g.close()
+    assert np.array_equal(out[0].view(np.uint32), out[1].view(np.uint32))
