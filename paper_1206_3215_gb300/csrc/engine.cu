@@ -17,6 +17,11 @@
 using namespace pss;
 
 namespace {
+// the device status word pass kernels report a lost tile copy in
+int *pass_status(pss_grid *g) { return reinterpret_cast<int *>(g->flags) + FLAG_SLOT_PASS_STATUS; }
+}  // namespace
+
+namespace {
 
 template <class Rl> V2<Rl> *B(pss_grid *g, int i) { return static_cast<V2<Rl> *>(g->buf[i]); }
 template <class Rl> const V2<Rl> *C(const void *p) { return static_cast<const V2<Rl> *>(p); }
@@ -312,8 +317,7 @@ template <class Rl> int nls_step(pss_grid *g, int64_t n)
     const Rl sdt = Rl(g->p.sigma * g->p.dt);
     auto col = [&](int full, Rl scale) {
         return nls_col_pass<Rl>(B<Rl>(g, 0), g->nx, g->ny, g->batch, scale, Tw<Rl>(g->ax[full]),
-                                Tw<Rl>(g->by[full]), Tw<Rl>(g->twy),
-                                reinterpret_cast<int *>(g->flags) + FLAG_SLOT_PASS_STATUS, g->stream);
+                                Tw<Rl>(g->by[full]), Tw<Rl>(g->twy), pass_status(g), g->stream);
     };
     if (n == 0) return PSS_OK;
     int rc;
@@ -515,7 +519,7 @@ template <class Rl> int sg_step(pss_grid *g, int64_t n)
             if ((rc = g->pass_end()) || (rc = g->cuda(e, "sg row pass (half spectrum)"))) return rc;
             if ((rc = g->pass_begin(1))) return rc;
             e = sg_col_pass<Rl>(h, u, d, g->sx, g->ny, g->batch, Rt<Rl>(g->kx2h), Rt<Rl>(g->ky2), Rl(g->p.dt),
-                                Tw<Rl>(g->twy), g->stream, g->nx);
+                                Tw<Rl>(g->twy), pass_status(g), g->stream, g->nx);
             if ((rc = g->pass_end()) || (rc = g->cuda(e, "sg column pass (half spectrum)"))) return rc;
         }
         return PSS_OK;
@@ -526,7 +530,7 @@ template <class Rl> int sg_step(pss_grid *g, int64_t n)
         if ((rc = g->pass_end()) || (rc = g->cuda(e, "sg row pass"))) return rc;
         if ((rc = g->pass_begin(1))) return rc;
         e = sg_col_pass<Rl>(B<Rl>(g, 2), B<Rl>(g, 0), B<Rl>(g, 1), g->nx, g->ny, g->batch, Rt<Rl>(g->kx2),
-                            Rt<Rl>(g->ky2), Rl(g->p.dt), Tw<Rl>(g->twy), g->stream);
+                            Rt<Rl>(g->ky2), Rl(g->p.dt), Tw<Rl>(g->twy), pass_status(g), g->stream);
         if ((rc = g->pass_end()) || (rc = g->cuda(e, "sg column pass"))) return rc;
     }
     return PSS_OK;

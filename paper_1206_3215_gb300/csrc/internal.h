@@ -50,9 +50,10 @@ cudaError_t sg_row_pass(V2<Rl> *h, int64_t nx, int64_t rows_total, const TW<Rl> 
 // Column pass: column FFT of S = F sin u^n; d <- d - (a u + dt^2 S)/(1 + a/4),
 // u <- u + d (a = dt^2 |k|^2), in place; H <- column inverse FFT of u / (nreal ny).
 // nx is the row stride (columns processed), nreal the real row length (0: nx).
+// *status gets STATUS_TMA_TIMEOUT if a tile copy never arrived.
 template <class Rl>
 cudaError_t sg_col_pass(V2<Rl> *h, V2<Rl> *u, V2<Rl> *d, int64_t nx, int64_t ny, int64_t batch,
-                        const Rl *kx2, const Rl *ky2, Rl dt, const TW<Rl> *twy, cudaStream_t s,
+                        const Rl *kx2, const Rl *ky2, Rl dt, const TW<Rl> *twy, int *status, cudaStream_t s,
                         int64_t nreal = 0);
 // Half-spectrum (real-to-complex) sine-Gordon row pass, k_sg_r2c.cu: rows of
 // stride sx holding kx = 0 .. nx/2; twm: twiddles of length nx/2, twn: of nx.

@@ -30,6 +30,17 @@ template <class Rl> __device__ __forceinline__ void phase_taylor(Rl a, Rl &sn, R
     cm1 = t2 * (Rl(-0.5) + t2 * (Rl(1.0 / 24) + t2 * (Rl(-1.0 / 720) + t2 * (Rl(1.0 / 40320) + t2 * Rl(-1.0 / 3628800)))));
 }
 
+// FP32 on |a| <= 1/64 (the workload's phases are ~1e-3): sin a = a - a^3/6 and
+// cos a - 1 = -a^2/2 + a^4/24, whose first omitted terms (a^5/120, a^6/720)
+// are below 1e-11 relative to the unit modulus, far under one FP32 rounding
+constexpr float phase_short_range() { return 1.0f / 64; }
+__device__ __forceinline__ void phase_short(float a, float &sn, float &cm1)
+{
+    const float t2 = a * a;
+    sn = __fmaf_rn(a * t2, -1.0f / 6, a);
+    cm1 = t2 * __fmaf_rn(t2, 1.0f / 24, -0.5f);
+}
+
 template <class Rl> __device__ __forceinline__ void phase_terms(Rl th, Rl &sn, Rl &cm1)
 {
     constexpr int KMAX = sizeof(Rl) == 4 ? 130 : 1026;
@@ -76,19 +87,31 @@ template <class Rl> struct NlsRow {
             // increment is formed without cancellation, so the modulus is
             // kept to the final rounding.  When every phase of this thread is
             // in the Taylor range (always, at the workload's dt |psi|^2), the
-            // straight-line Taylor code runs; the halving path is out of line.
+            // straight-line Taylor code runs (FP32: the short sums below
+            // 1/64); the halving path is out of line.
             Rl big = Rl(0);
 #pragma unroll
             for (int m = 0; m < P; ++m) big = fmax(big, fabs(sigma_dt * (v[m].x * v[m].x + v[m].y * v[m].y)));
-            if (big <= phase_taylor_range<Rl>()) {
+            auto apply = [&](auto terms) {
 #pragma unroll
                 for (int m = 0; m < P; ++m) {
                     const Rl x = v[m].x, y = v[m].y;
                     Rl sn, cm1;
-                    phase_taylor(sigma_dt * (x * x + y * y), sn, cm1);
+                    terms(sigma_dt * (x * x + y * y), sn, cm1);
                     v[m].x = x + (x * cm1 + y * sn);
                     v[m].y = y + (y * cm1 - x * sn);
                 }
+            };
+            // one straight-line body (FP32: the short sums; FP64: the Taylor
+            // sums) and the general path, so the code stays small
+            bool fast;
+            if constexpr (sizeof(Rl) == 4) fast = big <= phase_short_range();
+            else fast = big <= phase_taylor_range<Rl>();
+            if (fast) {
+                apply([](Rl a, Rl &sn, Rl &cm1) {
+                    if constexpr (sizeof(Rl) == 4) phase_short(a, sn, cm1);
+                    else phase_taylor(a, sn, cm1);
+                });
             } else {
 #pragma unroll
                 for (int m = 0; m < P; ++m) {

@@ -72,7 +72,8 @@ template <class Rl> struct SgCol {
     const Rl *kx2, *ky2;
     Rl dt2, inv_n2;     // dt^2, 1/(nx ny)
     int64_t nx;
-    __device__ const V2<Rl> *in(int) const { return h; }
+    int *status;        // set when a tile copy did not arrive
+    __host__ __device__ const V2<Rl> *in(int) const { return h; }
     template <int N, int P, bool BLOCK, class Sm>
     __device__ __forceinline__ void col(V2<Rl> (&vv)[1][P], int64_t field, int x, int t,
                                         const Sm (&sm)[1], const TW<Rl> *tw) const
@@ -154,16 +155,18 @@ cudaError_t sg_row_pass(V2<Rl> *h, int64_t nx, int64_t rows_total, const TW<Rl> 
 // row of the real-space field (nx for full spectra, more for half spectra)
 template <class Rl>
 cudaError_t sg_col_pass(V2<Rl> *h, V2<Rl> *u, V2<Rl> *d, int64_t nx, int64_t ny, int64_t batch,
-                        const Rl *kx2, const Rl *ky2, Rl dt, const TW<Rl> *twy, cudaStream_t s, int64_t nreal)
+                        const Rl *kx2, const Rl *ky2, Rl dt, const TW<Rl> *twy, int *status, cudaStream_t s,
+                        int64_t nreal)
 {
-    SgCol<Rl> op{h, u, d, kx2, ky2, dt * dt, Rl(1.0 / (double(nreal > 0 ? nreal : nx) * double(ny))), nx};
+    SgCol<Rl> op{h, u, d, kx2, ky2, dt * dt, Rl(1.0 / (double(nreal > 0 ? nreal : nx) * double(ny))), nx, status};
     return launch_col<Rl>(ny, nx, op, twy, batch, s);
 }
 
 #define PSS_INST(Rl)                                                                              \
     template cudaError_t sg_row_pass<Rl>(V2<Rl> *, int64_t, int64_t, const TW<Rl> *, cudaStream_t); \
     template cudaError_t sg_col_pass<Rl>(V2<Rl> *, V2<Rl> *, V2<Rl> *, int64_t, int64_t, int64_t,   \
-                                         const Rl *, const Rl *, Rl, const TW<Rl> *, cudaStream_t, int64_t);
+                                         const Rl *, const Rl *, Rl, const TW<Rl> *, int *, cudaStream_t, \
+                                         int64_t);
 PSS_INST(float)
 PSS_INST(double)
 
