@@ -118,13 +118,10 @@ inline bool tma_enabled()
     return !(e && e[0] == '0' && e[1] == 0);
 }
 
-// Tensor-copy staging is used up to N = 1024: beyond, the kernel spills
-// 130 - 230 bytes per thread where the per-point staging kernel spills
-// at most 48 (ptxas, FP32, 128 registers).
 template <class Rl, int N, class Op> constexpr bool tma_col()
 {
     using C = ColCfgOf<Rl, N, Op, 0>;
-    return TmaCol<Op>::value && sizeof(Rl) == 4 && C::BLOCK && C::NBUF == 1 && N >= 256 && N <= 1024 &&
+    return TmaCol<Op>::value && sizeof(Rl) == 4 && C::BLOCK && C::NBUF == 1 && N >= 256 &&
            (C::W * sizeof(V2<Rl>)) % 16 == 0;
 }
 

@@ -424,7 +424,10 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, 
     using Sm = SmemLine<V, C::PADLOG>;
     static_assert(C::NBUF == 1, "one staging buffer");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *const buf = reinterpret_cast<V *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    // align to 128 bytes by an offset from the shared array itself (an
+    // address rebuilt from an integer would lose the shared state space and
+    // turn every exchange access into a generic one)
+    V *const buf = reinterpret_cast<V *>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
     const unsigned sbar = smem_addr(buf + C::BUF);
     const int c = threadIdx.x % C::W, t = threadIdx.x / C::W;
     // 32-bit tile counters (the launcher checks the count): fewer live registers

@@ -76,7 +76,7 @@ def test_autotune_keeps_state_and_one_plan_per_key(lib, cuda_device, eq):
         assert np.array_equal(a[0], b[1])
 
 
-@pytest.mark.parametrize("n", [256, 512, 1024])
+@pytest.mark.parametrize("n", [256, 512, 1024, 2048, 4096])
 def test_tensor_copy_staging_is_bitwise_equal(lib, cuda_device, monkeypatch, n):
     # The NLS column pass stages its tiles by one tensor copy each (PSS_TMA
     # unset) or by per-point copies (PSS_TMA=0): the arithmetic is the same,
@@ -94,3 +94,23 @@ def test_tensor_copy_staging_is_bitwise_equal(lib, cuda_device, monkeypatch, n):
         out.append(g.get_state())
         g.close()
     assert np.array_equal(out[0].view(np.uint32), out[1].view(np.uint32))
+
+
+@pytest.mark.parametrize("rfft", [0, 1])
+def test_tensor_copy_staging_is_bitwise_equal_sg(lib, cuda_device, monkeypatch, rfft):
+    # the sine-Gordon column pass, also on half spectra (rows of nx/2 + 8
+    # columns: a row stride that is not a power of two)
+    n, Ls = 2048, 10 * math.pi
+    u0, v0 = S.sg_gaussian(n, batch=2)
+    out = []
+    for tma in ("1", "0"):
+        monkeypatch.setenv("PSS_TMA", tma)
+        monkeypatch.setenv("PSS_PLAN", "0")
+        g = lib.Grid("sg", n, "fp32", batch=2, lx=Ls, ly=Ls, x0=-Ls / 2, y0=-Ls / 2, dt=1e-3, rfft=rfft)
+        g.set_state(u0, v0)
+        g.step(5)
+        g.sync()
+        out.append(g.get_state())
+        g.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(np.ascontiguousarray(a).view(np.uint8), np.ascontiguousarray(b).view(np.uint8))
