@@ -150,8 +150,9 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
     // with 3|mx| >= nx, which the mask keeps at zero in w, J and the
     // derivative fields; the pass does not visit them (0, 0 without dealiasing)
     int64_t skip_lo, skip_n;
+    int *status;  // set when a tile copy did not arrive
     static constexpr bool midpoint = MID;  // implicit midpoint, else trapezoidal Jacobian
-    __device__ const V2<Rl> *in(int) const { return c1; }
+    __host__ __device__ const V2<Rl> *in(int) const { return c1; }
     __device__ V2<Rl> *wb(int b) const { return b == 0 ? w0 : b == 1 ? w1 : w2; }
     // field whose derivatives feed the next Jacobian: w^{k+1}, or the
     // midpoint (w^{k+1} + w^n)/2
@@ -385,7 +386,7 @@ cudaError_t ns_col_run(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, v
     using Op = NsCol<Rl, MID, HALF>;
     Op op{c1, c2, w[0], w[1], w[2], jn, static_cast<NsField *>(fs), partials, kxo, kyo, kx2, ky2,
           keepx, keepy, Rl(0.5 * dt), Rl(0.5 * dt * nu), Rl(1.0 / (double(nxf) * double(ny))), sx, ctl, 0,
-          nxf, 0, 0};
+          nxf, 0, 0, const_cast<int *>(ctl) + FLAG_SLOT_PASS_STATUS};
     switch (ny) {
 #define PSS_CASE(N)                                                                          \
     case N:                                                                                  \

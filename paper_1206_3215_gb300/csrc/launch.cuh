@@ -135,11 +135,12 @@ inline cudaError_t launch_col_tma(Op op, const TW<Rl> *tw, int64_t nx, int64_t b
     static int ctas[32] = {};
     cudaError_t e = allow_smem(k, smem, done);
     if (e != cudaSuccess) return e;
-    const int64_t tiles = (nx / C::W) * batch;
+    const int64_t tiles = kept_groups(op, nx / C::W) * batch;
     if (tiles <= 0) return cudaSuccess;
     if (tiles > INT32_MAX - 2 * 65536) return cudaErrorInvalidValue;  // the kernel counts tiles in 32 bits
     CUtensorMap map;
-    if ((e = encode_col_map(&map, op.in(0), int(sizeof(V2<Rl>)), nx, N, batch, C::W)) != cudaSuccess) return e;
+    if ((e = encode_col_map(&map, op.in(0), int(sizeof(V2<Rl>)), in_stride(op, nx), N, batch, C::W)) != cudaSuccess)
+        return e;
     int grid = 0;
     if ((e = resident_ctas(k, C::THREADS, smem, ctas, &grid)) != cudaSuccess) return e;
     if (tiles < grid) grid = int(tiles);

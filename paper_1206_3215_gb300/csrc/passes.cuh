@@ -320,7 +320,7 @@ template <class Op> __device__ __forceinline__ auto col_in(const Op &op, int k, 
 template <class Op, class = void> struct HasInStride : std::false_type {};
 template <class Op>
 struct HasInStride<Op, std::void_t<decltype(std::declval<const Op &>().in_stride)>> : std::true_type {};
-template <class Op> __device__ __forceinline__ int64_t in_stride(const Op &op, int64_t nx)
+template <class Op> __host__ __device__ __forceinline__ int64_t in_stride(const Op &op, int64_t nx)
 {
     if constexpr (HasInStride<Op>::value) return op.in_stride;
     else return nx;
@@ -398,8 +398,9 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, VAR>::THREADS, ColCfgOf<Rl
 
 // ----------------------------------------------------------------------------
 // Column pass whose tiles arrive by one tensor copy each (see tma.cuh): for
-// ops with one input array of row stride nx that visit every column group and
-// name a status word (op.status).  The tile lands as a dense [N][W] block at
+// ops with one input array (the same for every field) that name a status
+// word (op.status); the input's row stride and the skipped column groups
+// follow in_stride() and group_index().  The tile lands as a dense [N][W] block at
 // the start of the buffer; thread (c, t) reads its points t + T m of column c
 // from there (a warp reads 32 consecutive points), and the padded column
 // lines of the same buffer then serve as the transforms' exchange space (the
@@ -407,8 +408,7 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, VAR>::THREADS, ColCfgOf<Rl
 template <class Op, class = void> struct TmaCol : std::false_type {};
 template <class Op>
 struct TmaCol<Op, std::void_t<decltype(std::declval<const Op &>().status)>>
-    : std::integral_constant<bool, Op::NIN == 1 && !FieldIn<Op>::value && !HasInStride<Op>::value &&
-                                       !SkipsGroups<Op>::value> {};
+    : std::integral_constant<bool, Op::NIN == 1 && !FieldIn<Op>::value> {};
 
 // dynamic shared memory of the tensor-copy column pass: the buffer, room to
 // align it to 128 bytes and the mbarrier
@@ -431,13 +431,13 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, 
     const unsigned sbar = smem_addr(buf + C::BUF);
     const int c = threadIdx.x % C::W, t = threadIdx.x / C::W;
     // 32-bit tile counters (the launcher checks the count): fewer live registers
-    const int groups = int(nx / C::W), tiles = groups * int(batch);
+    const int groups = int(kept_groups(op, nx / C::W)), tiles = groups * int(batch);
     if (threadIdx.x == 0) mbar_init(sbar, 1);
     __syncthreads();
     unsigned parity = 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, parity ^= 1u) {
         const int field = tile / groups;
-        const int x0 = (tile - field * groups) * C::W;
+        const int x0 = int(group_index(op, tile - field * groups)) * C::W;
         if (threadIdx.x == 0) {
             fence_proxy_async_smem();  // the previous tile's shared-memory accesses come first
             mbar_arrive_expect_tx(sbar, unsigned(N * C::W * sizeof(V)));
