@@ -158,9 +158,8 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# files that define the NLS pass kernels (and their launch shapes)
 # sources the NLS pass kernels are compiled from (declarations-only headers excluded)
-NLS_KERNEL_FILES = ("fft_core.cuh", "passes.cuh", "launch.cuh", "k_nls.cu")
+NLS_KERNEL_FILES = ("fft_core.cuh", "passes.cuh", "launch.cuh", "tma.cuh", "k_nls.cu")
 
 
 def kernel_source_hash(files=NLS_KERNEL_FILES) -> str:
@@ -456,8 +455,9 @@ def run_ours(args):
     dn, dms = (cols_n, cols_ms) if dom == "col" else (rows_n, rows_ms)
     achieved = bytes_per_pass / (dms / dn / 1e3) / 1e9 if dn else None
     # launch shape 0 (the autotuner keeps it for these passes; if it changed
-    # a plan, the recorded counters are not for the kernels that ran)
-    kernel_name = {"col": "k_col<float, 1024, NlsCol<float>, 0>", "row": "k_row<float, 1024, NlsRow<float>, 0>"}[dom]
+    # a plan, the recorded counters are not for the kernels that ran); the
+    # column pass of shape 0 stages its tiles by tensor copies
+    kernel_name = {"col": "k_col_tma<float, 1024, NlsCol<float>>", "row": "k_row<float, 1024, NlsRow<float>, 0>"}[dom]
     traffic = ncu_traffic(kernel_name) if plans_changed == 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
