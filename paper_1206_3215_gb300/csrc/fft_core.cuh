@@ -243,16 +243,25 @@ template <bool BLOCK> __device__ __forceinline__ void fft_sync()
     else __syncwarp();
 }
 
+// A transform's caller may pass a hook that runs once, at the start of the
+// last stage: by then this thread has made its last shared-memory access of
+// the transform, so a pass can start refilling the buffer for its next tile
+// while the last stage computes.
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
 // One Stockham stage s of a length-N transform (DIR = -1 forward, +1 inverse).
 // On entry register m holds element t + T m of the stage input; on exit (for
 // the last stage) register m holds output element t + T m.  Other stages leave
 // their output in shared memory and reload the next stage's input.
-template <int N, int P, int DIR, int S, bool BLOCK, class V, class Sm, class W>
-__device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const W *__restrict__ tw)
+template <int N, int P, int DIR, int S, bool BLOCK, class V, class Sm, class W, class H>
+__device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const W *__restrict__ tw, const H &hook)
 {
     using PL = Plan<N, P>;
     constexpr int R = PL::radix(S), NS = PL::span(S), T = PL::T, Q = P / R;
     constexpr bool LAST = (S == PL::STAGES - 1);
+    if constexpr (LAST) hook();
     if constexpr (S > 0) {
         // twiddles W_{NS R}^{(j mod NS) r} = W_N^{(j mod NS) r N/(NS R)}
         tw = launder(tw);
@@ -293,21 +302,22 @@ __device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const 
     }
 }
 
-template <int N, int P, int DIR, int S, bool BLOCK, class V, class Sm, class W>
-__device__ __forceinline__ void fft_stages(V (&v)[P], const Sm &sm, int t, const W *__restrict__ tw)
+template <int N, int P, int DIR, int S, bool BLOCK, class V, class Sm, class W, class H>
+__device__ __forceinline__ void fft_stages(V (&v)[P], const Sm &sm, int t, const W *__restrict__ tw, const H &hook)
 {
     if constexpr (S < Plan<N, P>::STAGES) {
-        fft_stage<N, P, DIR, S, BLOCK>(v, sm, t, tw);
-        fft_stages<N, P, DIR, S + 1, BLOCK>(v, sm, t, tw);
+        fft_stage<N, P, DIR, S, BLOCK>(v, sm, t, tw, hook);
+        fft_stages<N, P, DIR, S + 1, BLOCK>(v, sm, t, tw, hook);
     }
 }
 
 // Full unnormalised length-N transform of the points held by the T threads
 // t = 0..T-1 (register m = element t + T m, in and out).
-template <int N, int P, int DIR, bool BLOCK, class V, class Sm, class W>
-__device__ __forceinline__ void block_fft(V (&v)[P], const Sm &sm, int t, const W *__restrict__ tw)
+template <int N, int P, int DIR, bool BLOCK, class V, class Sm, class W, class H = NoHook>
+__device__ __forceinline__ void block_fft(V (&v)[P], const Sm &sm, int t, const W *__restrict__ tw,
+                                          const H &hook = H{})
 {
-    fft_stages<N, P, DIR, 0, BLOCK>(v, sm, t, tw);
+    fft_stages<N, P, DIR, 0, BLOCK>(v, sm, t, tw, hook);
 }
 
 }  // namespace pss

@@ -71,12 +71,13 @@ template <class Rl> struct NlsRow {
     static constexpr int NIN = 1;
     static constexpr bool LEAN = true;
     static constexpr int PMAX = 32;
+    static constexpr bool EARLY_NEXT = true;
     V2<Rl> *data;
     Rl sigma_dt;
     __device__ const V2<Rl> *in(int) const { return data; }
-    template <int N, int P, bool BLOCK, class Sm>
+    template <int N, int P, bool BLOCK, class Sm, class H = NoHook>
     __device__ __forceinline__ void row(V2<Rl> (&vv)[1][P], int64_t row, bool ok, int t,
-                                        const Sm (&smm)[1], const TW<Rl> *tw) const
+                                        const Sm (&smm)[1], const TW<Rl> *tw, const H &hook = H{}) const
     {
         constexpr int T = N / P;
         V2<Rl>(&v)[P] = vv[0];
@@ -127,7 +128,9 @@ template <class Rl> struct NlsRow {
             conj_all(v);
 #pragma unroll 1
             for (int pass = 0; pass < 2; ++pass) {
-                block_fft<N, P, -1, BLOCK>(v, sm, t, tw);
+                block_fft<N, P, -1, BLOCK>(v, sm, t, tw, [&]() {
+                    if (pass == 1) hook();
+                });
                 if (pass == 0) {
                     conj_all(v);
                     nonlinear();
@@ -138,7 +141,7 @@ template <class Rl> struct NlsRow {
             fence(v);
             nonlinear();
             fence(v);
-            block_fft<N, P, -1, BLOCK>(v, sm, t, tw);
+            block_fft<N, P, -1, BLOCK>(v, sm, t, tw, hook);
         }
         store_line<P, T>(v, p, 1, t, ok);
     }

@@ -255,6 +255,14 @@ __device__ __forceinline__ void read_line(V (&v)[P], const Sm &sm, int t)
 // ----------------------------------------------------------------------------
 // Kernel shells
 
+// An op that sets EARLY_NEXT takes a hook as the last argument of row() and
+// calls it once its last transform has made its last shared-memory access
+// (block_fft's hook): a single-buffered row pass then issues the copies of
+// its next tile there, under the rest of the tile's arithmetic and stores.
+template <class Op, class = void> struct EarlyNext : std::false_type {};
+template <class Op>
+struct EarlyNext<Op, std::void_t<decltype(Op::EARLY_NEXT)>> : std::integral_constant<bool, Op::EARLY_NEXT> {};
+
 // rows_total = batch * ny; row r of the batch starts at element r * NX
 template <class Rl, int N, class Op, int VAR>
 __global__ void __launch_bounds__(RowCfgOf<Rl, N, Op, VAR>::THREADS, RowCfgOf<Rl, N, Op, VAR>::MIN_CTAS)
@@ -278,14 +286,17 @@ __global__ void __launch_bounds__(RowCfgOf<Rl, N, Op, VAR>::THREADS, RowCfgOf<Rl
         cp_async_commit();
     };
 
+    constexpr bool EARLY = EarlyNext<Op>::value && C::NBUF == 1;
     int64_t tile = blockIdx.x;
-    if (C::NBUF == 2) issue(tile, 0);
+    if (C::NBUF == 2 || EARLY) issue(tile, 0);
     for (int it = 0; tile < tiles; ++it, tile += gridDim.x) {
         int b = 0;
         if constexpr (C::NBUF == 2) {
             b = it & 1;
             issue(tile + gridDim.x, b ^ 1);
             cp_async_wait<1>();
+        } else if constexpr (EARLY) {
+            cp_async_wait<0>();  // issued during the previous tile (or above)
         } else {
             issue(tile, 0);
             cp_async_wait<0>();
@@ -298,8 +309,17 @@ __global__ void __launch_bounds__(RowCfgOf<Rl, N, Op, VAR>::THREADS, RowCfgOf<Rl
             sm[k] = line(b, k);
             read_line<C::P, C::T>(v[k], sm[k], t);
         }
-        op.template row<N, C::P, C::BLOCK>(v, row, row < rows_total, t, sm, tw);
-        fft_sync<C::BLOCK>();  // this buffer is refilled by the next iteration's prefetch
+        if constexpr (EARLY) {
+            const int64_t next = tile + gridDim.x;
+            const auto hook = [&]() {
+                fft_sync<C::BLOCK>();  // the row's last shared-memory reads are done
+                issue(next, 0);
+            };
+            op.template row<N, C::P, C::BLOCK>(v, row, row < rows_total, t, sm, tw, hook);
+        } else {
+            op.template row<N, C::P, C::BLOCK>(v, row, row < rows_total, t, sm, tw);
+            fft_sync<C::BLOCK>();  // this buffer is refilled by the next iteration's prefetch
+        }
     }
     cp_async_wait<0>();
 }
