@@ -35,18 +35,21 @@ template <class Rl> struct SgRow {
     static constexpr int NIN = 1;
     static constexpr bool LEAN = sg_shared(sizeof(Rl));
     static constexpr int PMAX = 32;
+    static constexpr bool EARLY_NEXT = true;
     V2<Rl> *h;  // in: H rows; out: S rows (in place)
     __device__ const V2<Rl> *in(int) const { return h; }
-    template <int N, int P, bool BLOCK, class Sm>
+    template <int N, int P, bool BLOCK, class Sm, class H = NoHook>
     __device__ __forceinline__ void row(V2<Rl> (&vv)[1][P], int64_t r, bool ok, int t, const Sm (&sm)[1],
-                                        const TW<Rl> *tw) const
+                                        const TW<Rl> *tw, const H &hook = H{}) const
     {
         V2<Rl>(&v)[P] = vv[0];
         if constexpr (sg_shared(sizeof(Rl))) {
             conj_all(v);
 #pragma unroll 1
             for (int pass = 0; pass < 2; ++pass) {
-                block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw);
+                block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw, [&]() {
+                    if (pass == 1) hook();
+                });
                 if (pass == 0)  // u = Re F^-1 H = Re conj(F conj H) = Re F conj H
 #pragma unroll
                     for (int m = 0; m < P; ++m) v[m] = V2<Rl>{sin_(v[m].x), Rl(0)};
@@ -57,7 +60,7 @@ template <class Rl> struct SgRow {
 #pragma unroll
             for (int m = 0; m < P; ++m) v[m] = V2<Rl>{sin_(v[m].x), Rl(0)};
             fence(v);
-            block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw);
+            block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw, hook);
         }
         store_line<P, N / P>(v, h + r * N, 1, t, ok);
     }
