@@ -272,6 +272,7 @@ int pss_grid::check_pass_status()
     *host_slot = 0;
     if ((rc = cuda(cudaMemsetAsync(dev_slot, 0, sizeof(int), stream), "status reset"))) return rc;
     has_state = false;
+    drop_graphs();  // captured launches are rebuilt by the next step
     return fail(PSS_E_CUDA, "a column-pass tile copy did not arrive in time; the state is lost (set it again)");
 }
 

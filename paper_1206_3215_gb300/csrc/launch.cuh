@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cstdlib>
+#include <cstring>
 
 #include "passes.cuh"
 #include "plan.h"
@@ -144,7 +145,13 @@ inline cudaError_t launch_col_tma(Op op, const TW<Rl> *tw, int64_t nx, int64_t b
     int grid = 0;
     if ((e = resident_ctas(k, C::THREADS, smem, ctas, &grid)) != cudaSuccess) return e;
     if (tiles < grid) grid = int(tiles);
-    k<<<dim3(unsigned(grid)), C::THREADS, smem, s>>>(map, op, tw, nx, batch);
+    // PSS_FAULT=tma_timeout: the tile copies are announced but not started and
+    // the wait is short, so every CTA gives up, sets the status word and
+    // returns (a bounded wait that runs out; nothing is left in flight)
+    const char *f = getenv("PSS_FAULT");
+    const bool inject = f && strcmp(f, "tma_timeout") == 0;
+    k<<<dim3(unsigned(grid)), C::THREADS, smem, s>>>(map, op, tw, nx, batch, inject ? 64u : TMA_WAIT_LIMIT,
+                                                      inject ? 1 : 0);
     return cudaGetLastError();
 }
 

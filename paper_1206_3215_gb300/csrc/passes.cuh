@@ -437,7 +437,7 @@ template <class C> constexpr size_t tma_col_smem() { return C::SMEM + 128 + 16; 
 template <class Rl, int N, class Op>
 __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, N, Op, 0>::MIN_CTAS)
     k_col_tma(const __grid_constant__ CUtensorMap map, Op op, const TW<Rl> *__restrict__ tw, int64_t nx,
-              int64_t batch)
+              int64_t batch, unsigned wait_limit, int skip_copy)
 {
     using C = ColCfgOf<Rl, N, Op, 0>;
     using V = V2<Rl>;
@@ -461,9 +461,11 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, 
         if (threadIdx.x == 0) {
             fence_proxy_async_smem();  // the previous tile's shared-memory accesses come first
             mbar_arrive_expect_tx(sbar, unsigned(N * C::W * sizeof(V)));
-            tma_load_4d(smem_addr(buf), &map, sbar, 2 * x0, 0, 0, field);
+            // skip_copy (host fault injection only): announce the bytes but
+            // start no copy, so that the wait below runs out with nothing in flight
+            if (!skip_copy) tma_load_4d(smem_addr(buf), &map, sbar, 2 * x0, 0, 0, field);
         }
-        const bool landed = mbar_wait(sbar, parity, TMA_WAIT_LIMIT);
+        const bool landed = mbar_wait(sbar, parity, wait_limit);
         if (__syncthreads_or(!landed)) {
             if (threadIdx.x == 0) atomicOr(op.status, STATUS_TMA_TIMEOUT);
             return;
