@@ -211,7 +211,10 @@ int pss_checkpoint_load(pss_grid *g, const void *buf, int where);
 int pss_set_profiling(pss_grid *g, int on);
 int pss_profile_read(pss_grid *g, double *out, int cap, int *count);
 
-/* Wait for all work enqueued on the grid's stream; reports deferred errors. */
+/* Wait for all work enqueued on the grid's stream; reports deferred errors:
+ * PSS_E_NOT_CONVERGED (NS), and PSS_E_CUDA when a column pass gave up waiting
+ * for one of its tile copies (its bounded wait ran out): the state is then
+ * lost and must be set again before the next step. */
 int pss_sync(pss_grid *g);
 
 /* Free every resource of the grid.  Safe on NULL. */
