@@ -237,10 +237,21 @@ template <int P, class V> __device__ __forceinline__ void conj_all(V (&v)[P])
     for (int m = 0; m < P; ++m) v[m].y = -v[m].y;
 }
 
-template <bool BLOCK> __device__ __forceinline__ void fft_sync()
+// Barrier among the threads that share a transform's shared-memory line.
+// SYNC = 0: the transform lives within one warp; SYNC = 1: it spans the
+// CTA; SYNC = G > 1 (a multiple of 32): the CTA holds several transforms of
+// G consecutive threads each (rows of a row pass), and each group waits only
+// for itself, on named barrier 1 + threadIdx.x / G.
+template <int SYNC> __device__ __forceinline__ void fft_sync()
 {
-    if constexpr (BLOCK) __syncthreads();
-    else __syncwarp();
+    if constexpr (SYNC == 0) {
+        __syncwarp();
+    } else if constexpr (SYNC == 1) {
+        __syncthreads();
+    } else {
+        static_assert(SYNC % 32 == 0, "whole warps per group");
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + int(threadIdx.x) / SYNC), "n"(SYNC) : "memory");
+    }
 }
 
 // A transform's caller may pass a hook that runs once, at the start of the
@@ -255,7 +266,7 @@ struct NoHook {
 // On entry register m holds element t + T m of the stage input; on exit (for
 // the last stage) register m holds output element t + T m.  Other stages leave
 // their output in shared memory and reload the next stage's input.
-template <int N, int P, int DIR, int S, bool BLOCK, class V, class Sm, class W, class H>
+template <int N, int P, int DIR, int S, int BLOCK, class V, class Sm, class W, class H>
 __device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const W *__restrict__ tw, const H &hook)
 {
     using PL = Plan<N, P>;
@@ -302,7 +313,7 @@ __device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const 
     }
 }
 
-template <int N, int P, int DIR, int S, bool BLOCK, class V, class Sm, class W, class H>
+template <int N, int P, int DIR, int S, int BLOCK, class V, class Sm, class W, class H>
 __device__ __forceinline__ void fft_stages(V (&v)[P], const Sm &sm, int t, const W *__restrict__ tw, const H &hook)
 {
     if constexpr (S < Plan<N, P>::STAGES) {
@@ -313,7 +324,7 @@ __device__ __forceinline__ void fft_stages(V (&v)[P], const Sm &sm, int t, const
 
 // Full unnormalised length-N transform of the points held by the T threads
 // t = 0..T-1 (register m = element t + T m, in and out).
-template <int N, int P, int DIR, bool BLOCK, class V, class Sm, class W, class H = NoHook>
+template <int N, int P, int DIR, int BLOCK, class V, class Sm, class W, class H = NoHook>
 __device__ __forceinline__ void block_fft(V (&v)[P], const Sm &sm, int t, const W *__restrict__ tw,
                                           const H &hook = H{})
 {

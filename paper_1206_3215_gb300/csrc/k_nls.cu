@@ -75,7 +75,7 @@ template <class Rl> struct NlsRow {
     V2<Rl> *data;
     Rl sigma_dt;
     __device__ const V2<Rl> *in(int) const { return data; }
-    template <int N, int P, bool BLOCK, class Sm, class H = NoHook>
+    template <int N, int P, int BLOCK, class Sm, class H = NoHook>
     __device__ __forceinline__ void row(V2<Rl> (&vv)[1][P], int64_t row, bool ok, int t,
                                         const Sm (&smm)[1], const TW<Rl> *tw, const H &hook = H{}) const
     {
@@ -168,7 +168,7 @@ template <class Rl> struct NlsCol {
     const TW<Rl> *ax, *by;  // exp(-i kx^2 tau) - 1, exp(-i ky^2 tau) - 1
     int *status;            // set when a tile copy did not arrive
     __host__ __device__ const V2<Rl> *in(int) const { return data; }
-    template <int N, int P, bool BLOCK, class Sm>
+    template <int N, int P, int BLOCK, class Sm>
     __device__ __forceinline__ void col(V2<Rl> (&vv)[1][P], int64_t field, int x, int t,
                                         const Sm (&smm)[1], const TW<Rl> *tw) const
     {

@@ -98,7 +98,7 @@ template <class Rl> struct NsRow {
                   // zero: the column pass skips them and the mask discards J there)
     int half;     // half spectra: only columns 0 .. nx/2 of J are read, so only they are written
     __device__ const V2<Rl> *in(int k) const { return k == 0 ? c1 : c2; }
-    template <int N, int P, bool BLOCK, class Sm>
+    template <int N, int P, int BLOCK, class Sm>
     __device__ __forceinline__ void row(V2<Rl> (&v)[2][P], int64_t r, bool ok, int t, const Sm (&sm)[2],
                                         const TW<Rl> *tw) const
     {
@@ -161,7 +161,7 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
         if constexpr (MID) return V2<Rl>{Rl(0.5) * (w1v.x + a_n.x), Rl(0.5) * (w1v.y + a_n.y)};
         return w1v;
     }
-    template <int N, int P, bool BLOCK, class Sm>
+    template <int N, int P, int BLOCK, class Sm>
     __device__ __forceinline__ void col(V2<Rl> (&vv)[1][P], int64_t field, int x, int t,
                                         const Sm (&sm)[1], const TW<Rl> *tw) const
     {
@@ -314,7 +314,7 @@ template <class Rl, bool HALF = false> struct NsPrep {
         const int b = fs ? fs[field].idx : 0;
         return b == 0 ? w0 : b == 1 ? w1 : w2;
     }
-    template <int N, int P, bool BLOCK, class Sm>
+    template <int N, int P, int BLOCK, class Sm>
     __device__ __forceinline__ void col(V2<Rl> (&vv)[1][P], int64_t field, int x, int t,
                                         const Sm (&sm)[1], const TW<Rl> *tw) const
     {

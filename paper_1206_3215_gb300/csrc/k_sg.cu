@@ -38,7 +38,7 @@ template <class Rl> struct SgRow {
     static constexpr bool EARLY_NEXT = true;
     V2<Rl> *h;  // in: H rows; out: S rows (in place)
     __device__ const V2<Rl> *in(int) const { return h; }
-    template <int N, int P, bool BLOCK, class Sm, class H = NoHook>
+    template <int N, int P, int BLOCK, class Sm, class H = NoHook>
     __device__ __forceinline__ void row(V2<Rl> (&vv)[1][P], int64_t r, bool ok, int t, const Sm (&sm)[1],
                                         const TW<Rl> *tw, const H &hook = H{}) const
     {
@@ -77,7 +77,7 @@ template <class Rl> struct SgCol {
     int64_t nx;
     int *status;        // set when a tile copy did not arrive
     __host__ __device__ const V2<Rl> *in(int) const { return h; }
-    template <int N, int P, bool BLOCK, class Sm>
+    template <int N, int P, int BLOCK, class Sm>
     __device__ __forceinline__ void col(V2<Rl> (&vv)[1][P], int64_t field, int x, int t,
                                         const Sm (&sm)[1], const TW<Rl> *tw) const
     {

@@ -31,7 +31,9 @@ template <class Rl, int M> struct R2cCfg {
     static constexpr int T = M / P;
     static constexpr int ROWS = T >= 256 ? 1 : 256 / T;
     static constexpr int THREADS = ROWS * T;
-    static constexpr bool BLOCK = THREADS > 32;
+    // barrier of one row's threads (fft_sync): a warp (T <= 32: the rows are
+    // warp-local), the CTA, or the row's own named barrier
+    static constexpr int BLOCK = T <= 32 ? 0 : (ROWS > 1 ? T : 1);
     static constexpr int PADLOG = pad_log(P);
     static constexpr int LINE = M + (M >> PADLOG) + 2;  // the padded line plus X_M
     static constexpr size_t SMEM = size_t(ROWS) * LINE * sizeof(V2<Rl>);

@@ -171,7 +171,9 @@ template <class Rl, int N, int NIN, bool LEAN = false, int PMAX = 32, int VAR = 
     static constexpr int PADLOG = pad_log(P);
     static constexpr int LINE = N + (N >> PADLOG);
     static constexpr int THREADS = ROWS * T;
-    static constexpr bool BLOCK = T > 32;
+    // barrier of one row's threads (fft_sync): a warp, the CTA, or the row's
+    // own named barrier when the CTA holds several multi-warp rows
+    static constexpr int BLOCK = T <= 32 ? 0 : (ROWS > 1 ? T : 1);
     // two buffers of NIN input lines per row (one when two do not fit)
     static constexpr int BUF = NIN * ROWS * LINE;
     static constexpr int MAXB = LEAN ? Shape<Rl>::MAX_NBUF : 2;
@@ -192,7 +194,7 @@ template <class Rl, int N, int NIN, bool LEAN = false, int PMAX = 32, int VAR = 
     static constexpr int PADLOG = pad_log(P);
     static constexpr int STRIDE = col_stride(N + (N >> PADLOG), W, Shape<Rl>::ESZ);
     static constexpr int THREADS = W * T;
-    static constexpr bool BLOCK = THREADS > 32;
+    static constexpr int BLOCK = THREADS > 32 ? 1 : 0;  // a column's threads span the CTA
     static constexpr int BUF = NIN * W * STRIDE;
     static constexpr int MAXB = LEAN ? Shape<Rl>::MAX_NBUF : 2;
     static constexpr int NBUF = (MAXB > 1 && size_t(2) * BUF * Shape<Rl>::ESZ <= SMEM_LIMIT) ? 2 : 1;
@@ -502,7 +504,7 @@ template <class Rl, int DIR> struct RowFft {
     V2<Rl> *data;
     Rl scale;  // applied after the transform when != 1
     __device__ const V2<Rl> *in(int) const { return data; }
-    template <int N, int P, bool BLOCK, class Sm>
+    template <int N, int P, int BLOCK, class Sm>
     __device__ __forceinline__ void row(V2<Rl> (&v)[1][P], int64_t r, bool ok, int t, const Sm (&sm)[1],
                                         const TW<Rl> *tw) const
     {
@@ -522,7 +524,7 @@ template <class Rl, int DIR> struct ColFft {
     int64_t nx;
     Rl scale;
     __device__ const V2<Rl> *in(int) const { return data; }
-    template <int N, int P, bool BLOCK, class Sm>
+    template <int N, int P, int BLOCK, class Sm>
     __device__ __forceinline__ void col(V2<Rl> (&v)[1][P], int64_t field, int x, int t,
                                         const Sm (&sm)[1], const TW<Rl> *tw) const
     {
