@@ -6,13 +6,17 @@
 // column index c fastest so that a warp's accesses cover 32/W rows of W
 // contiguous points.
 //
-// Both are persistent: each CTA walks tiles blockIdx.x, +gridDim.x, ...  While
-// it transforms one tile, cp.async copies of the next tile's input lines are
-// in flight into the other of two shared-memory buffers, so HBM stays busy
-// during the arithmetic without holding the data in registers.  Each thread
-// copies exactly the points it reads back for the first Stockham stage
-// (element t + T m of its line), so it only waits for its own copies; the
-// buffer then serves as the exchange space of that tile's transforms.
+// Both are persistent: each CTA walks tiles blockIdx.x, +gridDim.x, ...  With
+// two shared-memory buffers, cp.async copies of the next tile's input lines
+// are in flight into one while the CTA transforms the tile in the other, so
+// HBM stays busy during the arithmetic without holding the data in
+// registers.  Each thread copies exactly the points it reads back for the
+// first Stockham stage (element t + T m of its line), so it only waits for
+// its own copies; the buffer then serves as the exchange space of that
+// tile's transforms.  The lean FP32 shape has one buffer per CTA and two
+// CTAs per SM: its row passes start the next tile's copies once the last
+// transform has made its last shared-memory access, and its column passes
+// take each tile by one tensor copy (k_col_tma, below).
 //
 // The equation-specific work is an "op": it names its staged input arrays
 // and, given the staged points in registers, does the transforms around its
