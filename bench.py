@@ -158,8 +158,9 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# sources the NLS pass kernels are compiled from (declarations-only headers excluded)
-NLS_KERNEL_FILES = ("fft_core.cuh", "passes.cuh", "launch.cuh", "tma.cuh", "k_nls.cu")
+# sources the NLS pass kernels are compiled from, and the tensor map their column
+# tiles are described by (declarations-only headers excluded)
+NLS_KERNEL_FILES = ("fft_core.cuh", "passes.cuh", "launch.cuh", "tma.cuh", "tma.cu", "k_nls.cu")
 
 
 def kernel_source_hash(files=NLS_KERNEL_FILES) -> str:
