@@ -163,6 +163,11 @@ def peaks():
 NLS_KERNEL_FILES = ("fft_core.cuh", "passes.cuh", "launch.cuh", "tma.cuh", "tma.cu", "k_nls.cu")
 
 
+# the kernels the roofline reports, by pass (launch shape 0; the column pass of
+# that shape stages its tiles by tensor copies); keys of profiles/traffic.json
+ROOFLINE_KERNELS = {"col": "k_col_tma<float, 1024, NlsCol<float>>", "row": "k_row<float, 1024, NlsRow<float>, 0>"}
+
+
 def kernel_source_hash(files=NLS_KERNEL_FILES) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1206_3215_gb300", "csrc")
@@ -458,7 +463,7 @@ def run_ours(args):
     # launch shape 0 (the autotuner keeps it for these passes; if it changed
     # a plan, the recorded counters are not for the kernels that ran); the
     # column pass of shape 0 stages its tiles by tensor copies
-    kernel_name = {"col": "k_col_tma<float, 1024, NlsCol<float>>", "row": "k_row<float, 1024, NlsRow<float>, 0>"}[dom]
+    kernel_name = ROOFLINE_KERNELS[dom]
     traffic = ncu_traffic(kernel_name) if plans_changed == 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
