@@ -27,8 +27,12 @@ _lib = None
 __all__ = [
     "build", "num_threads", "fft1d", "dft1d", "fft2d", "ifft2d", "wavenumbers",
     "nls_run", "nls_invariants", "sg_init", "sg_run", "sg_fields", "sg_hamiltonian",
-    "ns_init", "ns_jacobian", "ns_run", "ns_field", "ns_invariants",
+    "ns_init", "ns_jacobian", "ns_run", "ns_field", "ns_invariants", "mutant",
 ]
+
+
+_CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+           "-ffp-contract=off"]
 
 
 def build(force: bool = False) -> str:
@@ -37,11 +41,36 @@ def build(force: bool = False) -> str:
         os.path.getmtime(p) > os.path.getmtime(_LIB) for p in (_SRC, _HDR))
     if force or stale:
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-               "-fno-fast-math", "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+        cmd = ["gcc"] + _CFLAGS + [_SRC, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def mutant(edits, workdir: str):
+    """A copy of this module bound to a deliberately broken oracle: the C
+    source with each (old, new) text edit applied (each `old` must occur
+    exactly once), compiled into `workdir`.  Used only by tests that check a
+    pin fails when a plausible mistake is planted in the oracle."""
+    import importlib.util
+    src = open(_SRC).read()
+    for old, new in edits:
+        if src.count(old) != 1:
+            raise ValueError(f"mutant edit target must occur once: {old!r}")
+        src = src.replace(old, new)
+    os.makedirs(workdir, exist_ok=True)
+    csrc = os.path.join(workdir, "pss_oracle_mutant.c")
+    with open(csrc, "w") as f:
+        f.write(src)
+    lib = os.path.join(workdir, "liboracle_mutant.so")
+    subprocess.run(["gcc"] + _CFLAGS + ["-I", _HERE, csrc, "-o", lib, "-lm"], check=True)
+    spec = importlib.util.spec_from_file_location(f"oracle_mutant_{abs(hash(src))}", __file__)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod._LIB = lib
+    mod._SRC = csrc
+    mod.build = lambda force=False: lib
+    return mod
 
 
 def _load():

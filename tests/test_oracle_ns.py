@@ -147,3 +147,123 @@ def test_midpoint_conserves_quadratic_invariants_inviscid(orc):
     w2, _, _ = orc.ns_run(wh, L, L, 0.0, dt, 20, tol=1e-24, max_iter=200, scheme="cn")
     c2, z2, e2 = orc.ns_invariants(w2, L, L)
     assert abs(z2 - z0) / z0 > 1e-9
+
+
+# --------------------------------------------------------------------------
+# The nonlinear term of the update (Section 4.3): its sign, and the
+# trapezoidal weighting (J^k + J^n)/2.  Taylor-Green has J = 0 and the
+# invariants above are blind to the sign of J, so these pins look at the
+# advection itself.
+
+# the oracle's Crank-Nicolson update with the trapezoidal Jacobian
+_CN_UPDATE = "wk1[i] = ((1.0 - a) * what[i] - 0.5 * dt * (jcur[i] + jn[i])) / (1.0 + a);"
+# plausible mistakes: J entered with the wrong sign; the newest iterate's J alone
+_MUTANTS = {
+    "j_sign": [(_CN_UPDATE, _CN_UPDATE.replace("- 0.5 * dt", "+ 0.5 * dt"))],
+    "jk_only": [(_CN_UPDATE, "wk1[i] = ((1.0 - a) * what[i] - dt * jcur[i]) / (1.0 + a);")],
+}
+
+
+def _two_mode(n):
+    L = 2 * math.pi
+    x = S.grid_coords(n, 0.0, L)
+    X, Y = np.meshgrid(x, x)
+    return L, X, Y, np.cos(X) + np.cos(2 * Y)
+
+
+def _initial_rate_errors(o, dts=(4e-3, 2e-3, 1e-3)):
+    # inviscid, omega0 = cos x + cos 2y: omega_t = -J = +1.5 sin x sin 2y at
+    # t = 0; the one-step difference quotient of a consistent scheme tends to
+    # it, with an error proportional to dt
+    n = 32
+    L, X, Y, w0 = _two_mode(n)
+    rate = 1.5 * np.sin(X) * np.sin(2 * Y)
+    wh0 = o.ns_init(w0, dealias=True)
+    errs = []
+    for dt in dts:
+        wh, _, ok = o.ns_run(wh0, L, L, 0.0, dt, 1, tol=1e-28, max_iter=500)
+        assert ok
+        errs.append(np.abs((o.ns_field(wh) - w0) / dt - rate).max())
+    return dts, errs
+
+
+def _rk4_reference(w0, n, L, nu, T, h):
+    """The semi-discrete 2/3-rule system d w_hat/dt = -D F[J] - nu |k|^2 w_hat
+    integrated by classical RK4 with numpy's FFT (an independent integrator:
+    fourth order, explicit, no fixed point), returned in physical space."""
+    k = np.fft.fftfreq(n, d=L / n) * 2 * np.pi
+    KX, KY = np.meshgrid(k, k)
+    K2 = KX ** 2 + KY ** 2
+    m = np.fft.fftfreq(n) * n
+    MX, MY = np.meshgrid(m, m)
+    D = ((3 * np.abs(MX) < n) & (3 * np.abs(MY) < n)).astype(float)
+
+    def rhs(wh):
+        ph = np.where(K2 > 0, wh / np.where(K2 > 0, K2, 1.0), 0.0)
+        px, py = np.fft.ifft2(1j * KX * ph).real, np.fft.ifft2(1j * KY * ph).real
+        wx, wy = np.fft.ifft2(1j * KX * wh).real, np.fft.ifft2(1j * KY * wh).real
+        return -D * np.fft.fft2(py * wx - px * wy) - nu * K2 * wh
+
+    wh = D * np.fft.fft2(w0)
+    for _ in range(int(round(T / h))):
+        a = rhs(wh)
+        b = rhs(wh + 0.5 * h * a)
+        c = rhs(wh + 0.5 * h * b)
+        d = rhs(wh + h * c)
+        wh = wh + h / 6 * (a + 2 * b + 2 * c + d)
+    return np.fft.ifft2(wh).real
+
+
+def _convergence_to_reference(o, n=32, nu=0.01, T=0.4, steps=(10, 20, 40)):
+    L = 2 * math.pi
+    w0 = S.ns_power_law(n)
+    ref = _rk4_reference(w0, n, L, nu, T, T / 800)
+    wh0 = o.ns_init(w0, dealias=True)
+    errs = []
+    for st in steps:
+        wh, _, ok = o.ns_run(wh0, L, L, nu, T / st, st, tol=1e-28, max_iter=500)
+        assert ok
+        errs.append(np.abs(o.ns_field(wh) - ref).max())
+    return errs, np.abs(ref).max()
+
+
+def _rate_pin_holds(o):
+    dts, errs = _initial_rate_errors(o)
+    first_order = all(1.8 <= errs[i] / errs[i + 1] <= 2.2 for i in range(len(errs) - 1))
+    return first_order and all(e <= 2.0 * dt for e, dt in zip(errs, dts))
+
+
+def _second_order_pin_holds(o):
+    errs, wmax = _convergence_to_reference(o)
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    return all(3.8 <= r <= 4.2 for r in ratios) and errs[-1] <= 1e-3 * wmax
+
+
+def test_update_advects_with_minus_jacobian(orc):
+    dts, errs = _initial_rate_errors(orc)
+    # measured: error / dt = 1.2 at every dt (half the second derivative)
+    for e, dt in zip(errs, dts):
+        assert e <= 2.0 * dt, (e, dt)
+    for i in range(len(errs) - 1):
+        assert 1.8 <= errs[i] / errs[i + 1] <= 2.2
+
+
+def test_trapezoidal_jacobian_is_second_order_against_rk4(orc):
+    # ratio 4 per halving of dt (measured 4.01, 4.00); J^k or J^n alone would
+    # be first order (ratio 2), a wrong sign converges to another solution
+    errs, wmax = _convergence_to_reference(orc)
+    for i in range(len(errs) - 1):
+        assert 3.8 <= errs[i] / errs[i + 1] <= 4.2, errs
+    assert errs[-1] <= 1e-3 * wmax, errs
+
+
+@pytest.mark.parametrize("name", sorted(_MUTANTS))
+def test_planted_update_mistakes_fail_the_pins(orc, tmp_path, name):
+    bad = orc.mutant(_MUTANTS[name], str(tmp_path))
+    rate_ok, order_ok = _rate_pin_holds(bad), _second_order_pin_holds(bad)
+    if name == "j_sign":
+        assert not rate_ok and not order_ok
+    else:  # consistent but first order: only the convergence pin sees it
+        assert not order_ok
+    # the unmodified oracle passes both
+    assert _rate_pin_holds(orc) and _second_order_pin_holds(orc)
