@@ -251,9 +251,12 @@ int pss_fft2d(void *data, int64_t nx, int64_t ny, int64_t batch, int precision, 
  * the process exits).  Every call shares that array: calls that overlap on
  * the GPU race on it, so serialise them (one stream, or events).  The first
  * call on each device looks up the array's device address with that device
- * current; make that first call before any stream capture.
+ * current (again after the device's context changes, e.g. after
+ * cudaDeviceReset); make that first call before any stream capture.
  * Errors: PSS_E_ARG (bad pointer, size, precision, or batch > 64, with a
- * message in pss_last_error(NULL)), PSS_E_CUDA. */
+ * message in pss_last_error(NULL)); PSS_E_CUDA if a CUDA error was already
+ * pending on entry (nothing is launched) or a launch fails (the message
+ * names which). */
 int pss_nls_invariants_static(const void *psi, const void *psi_hat, int64_t nx, int64_t ny,
                               int64_t batch, double lx, double ly, double sigma, int precision,
                               double *out, void *stream);

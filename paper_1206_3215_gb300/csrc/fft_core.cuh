@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace pss {
@@ -262,6 +264,57 @@ struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
 
+// FP32 transforms read the twiddles of their second stage (span NS = P,
+// radix R: NS (R - 1) values W_{NS R}^{jm r}) from a copy in shared memory
+// laid out [r - 1][jm], so that the threads of a warp, whose jm are
+// consecutive (or equal), read consecutive 16-byte words: no bank conflicts,
+// and shared-memory latency instead of a global load's.  Every kernel that
+// runs a FP32 transform of length N fills the copy once (fill_stage_tw) and
+// synchronises before its first transform.  PSS_SMEM_TW=0 reads every stage
+// from the global table instead.
+#ifndef PSS_SMEM_TW
+#define PSS_SMEM_TW 1
+#endif
+template <int N, int P> struct StageTw {
+    using PL = Plan<N, P>;
+    static constexpr bool ON = PSS_SMEM_TW && PL::STAGES >= 2;
+    static constexpr int NS = ON ? PL::span(1) : 1, R = ON ? PL::radix(1) : 2;
+    static constexpr int COUNT = NS * (R - 1);
+};
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+// a 16-byte shared-memory load kept in program order
+__device__ __forceinline__ float4 lds_f4(unsigned addr)
+{
+    float4 r;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "r"(addr));
+    return r;
+}
+// the copy of one (span, radix): a static shared array of the kernel
+template <int NS, int R> __device__ __forceinline__ float4 *stage_tw_smem()
+{
+    __shared__ __align__(16) float4 cache[NS * (R - 1)];
+    return cache;
+}
+// all threads of the CTA: copy the second stage's twiddles of a length-N
+// transform from the global table; the caller synchronises afterwards
+template <int N, int P> __device__ __forceinline__ void fill_stage_tw(const float4 *__restrict__ tw)
+{
+    using ST = StageTw<N, P>;
+    if constexpr (ST::ON) {
+        float4 *c = stage_tw_smem<ST::NS, ST::R>();
+        for (int e = int(threadIdx.x); e < ST::COUNT; e += int(blockDim.x)) {
+            const int r = e / ST::NS + 1, jm = e % ST::NS;
+            c[e] = __ldg(tw + jm * r * (N / (ST::NS * ST::R)));
+        }
+    }
+}
+template <int N, int P> __device__ __forceinline__ void fill_stage_tw(const double2 *) {}
+
 // One Stockham stage s of a length-N transform (DIR = -1 forward, +1 inverse).
 // On entry register m holds element t + T m of the stage input; on exit (for
 // the last stage) register m holds output element t + T m.  Other stages leave
@@ -275,14 +328,32 @@ __device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const 
     if constexpr (LAST) hook();
     if constexpr (S > 0) {
         // twiddles W_{NS R}^{(j mod NS) r} = W_N^{(j mod NS) r N/(NS R)}
+        constexpr bool SMEM = S == 1 && std::is_same<W, float4>::value && StageTw<N, P>::ON;
         tw = launder(tw);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int jm = (t + q * T) & (NS - 1);
+            if constexpr (SMEM) {
+                static_assert(NS == StageTw<N, P>::NS && R == StageTw<N, P>::R, "stage 1 shape");
+                // TWD loads in flight, issued in order (volatile loads are not
+                // hoisted further, so at most TWD twiddles occupy registers)
+                constexpr int TWD = 4;
+                const unsigned a0 = smem_u32(stage_tw_smem<NS, R>()) + unsigned(jm) * 16u;
+                float4 ring[TWD];
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const W w = __ldg(tw + jm * r * (N / (NS * R)));
-                v[q + r * Q] = twmul<DIR>(v[q + r * Q], w);
+                for (int r = 1; r < R && r <= TWD; ++r) ring[r - 1] = lds_f4(a0 + unsigned((r - 1) * NS) * 16u);
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    const float4 w = ring[(r - 1) % TWD];
+                    if (r + TWD < R) ring[(r - 1) % TWD] = lds_f4(a0 + unsigned((r + TWD - 1) * NS) * 16u);
+                    v[q + r * Q] = twmul<DIR>(v[q + r * Q], w);
+                }
+            } else {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    const W w = __ldg(tw + jm * r * (N / (NS * R)));
+                    v[q + r * Q] = twmul<DIR>(v[q + r * Q], w);
+                }
             }
         }
     }

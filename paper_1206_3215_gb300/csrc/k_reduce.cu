@@ -7,6 +7,7 @@
 #include <math.h>
 
 #include <cmath>
+#include <cstdio>
 #include <mutex>
 
 #include "fft_core.cuh"
@@ -209,24 +210,54 @@ static __device__ __align__(256) double g_static_scratch[STATIC_DOUBLES];
 
 namespace {
 std::mutex g_static_mu;
-double *g_static_addr[64] = {};  // device address of g_static_scratch per device ordinal
+// device address of g_static_scratch per device ordinal, with the context it
+// was looked up in (a cudaDeviceReset gives the device a new primary context,
+// in which the module and its array are loaded again)
+struct StaticAddr {
+    void *ctx = nullptr;
+    double *ptr = nullptr;
+};
+StaticAddr g_static_addr[64];
+
+// the driver's cuCtxGetCurrent, looked up once through the runtime (the
+// library does not link the driver library itself)
+using CtxGetCurrent = int (*)(void **);
+CtxGetCurrent ctx_get_current()
+{
+    static const CtxGetCurrent fn = []() -> CtxGetCurrent {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q);
+        return (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ? reinterpret_cast<CtxGetCurrent>(p) : nullptr;
+    }();
+    return fn;
+}
 
 // Host code sees g_static_scratch only as a host-side stand-in; the device
-// address is looked up once per device, with that device current.
+// address is looked up once per device and context, with that device current.
 cudaError_t static_scratch(double **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const CtxGetCurrent get = ctx_get_current();
+    if (!get) return cudaErrorNotSupported;
+    void *ctx = nullptr;
+    if (get(&ctx) != 0) return cudaErrorUnknown;
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_addr[dev]) {
+    StaticAddr &a = g_static_addr[dev];
+    if (!a.ptr || !ctx || a.ctx != ctx) {
+        // the lookup also makes the device's primary context current if no
+        // context was yet; the handle is read again after it
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
-        g_static_addr[dev] = static_cast<double *>(p);
+        if (get(&ctx) != 0 || !ctx) return cudaErrorUnknown;
+        a.ptr = static_cast<double *>(p);
+        a.ctx = ctx;
     }
-    *out = g_static_addr[dev];
+    *out = a.ptr;
     return cudaSuccess;
 }
 
@@ -291,6 +322,12 @@ extern "C" int pss_nls_invariants_static(const void *psi, const void *psi_hat, i
                          "library's static scratch");
         return 1;  // PSS_E_ARG
     }
+    // an error left pending by earlier, unrelated work on this thread would
+    // otherwise be reported (and cleared) as this call's launch failure
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        set_global_error("pss_nls_invariants_static: a CUDA error was already pending before the call");
+        return 3;  // PSS_E_CUDA
+    }
     double *scratch = nullptr;
     if (static_scratch(&scratch) != cudaSuccess) {
         set_global_error("pss_nls_invariants_static: cudaGetSymbolAddress failed");
@@ -302,6 +339,13 @@ extern "C" int pss_nls_invariants_static(const void *psi, const void *psi_hat, i
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double two_pi = 6.283185307179586476925286766559;
     const dim3 grid(RED_BLOCKS, unsigned(batch));
+    auto launched = [](const char *what) {
+        if (cudaGetLastError() == cudaSuccess) return true;
+        char msg[128];
+        snprintf(msg, sizeof msg, "pss_nls_invariants_static: launch of %s failed", what);
+        set_global_error(msg);
+        return false;
+    };
     if (precision == 0)
         k_nls_sums_inline<float><<<grid, RED_THREADS, 0, s>>>(
             static_cast<const float2 *>(psi), static_cast<const float2 *>(psi_hat), nx, ny,
@@ -310,12 +354,11 @@ extern "C" int pss_nls_invariants_static(const void *psi, const void *psi_hat, i
         k_nls_sums_inline<double><<<grid, RED_THREADS, 0, s>>>(
             static_cast<const double2 *>(psi), static_cast<const double2 *>(psi_hat), nx, ny,
             two_pi / lx, two_pi / ly, partials);
+    if (!launched("the block sums")) return 3;  // PSS_E_CUDA
     k_fold<3><<<unsigned(batch), RED_THREADS, 0, s>>>(partials, sums);
+    if (!launched("the fold")) return 3;
     k_nls_finish<<<1, 64, 0, s>>>(sums, batch, (lx / double(nx)) * (ly / double(ny)),
                                   1.0 / (double(nx) * double(ny)), sigma, out);
-    if (cudaGetLastError() != cudaSuccess) {
-        set_global_error("pss_nls_invariants_static: launch failed");
-        return 3;  // PSS_E_CUDA
-    }
+    if (!launched("the final scaling")) return 3;
     return 0;
 }

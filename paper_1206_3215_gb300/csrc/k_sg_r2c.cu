@@ -54,6 +54,8 @@ __global__ void __launch_bounds__(R2cCfg<Rl, M>::THREADS, R2cCfg<Rl, M>::MIN_CTA
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int rl = threadIdx.x / T, t = threadIdx.x % T;
     const Sm sm{reinterpret_cast<V *>(smem_raw) + rl * C::LINE};
+    fill_stage_tw<M, P>(twm);
+    __syncthreads();
     for (int64_t r0 = int64_t(blockIdx.x) * C::ROWS; r0 < rows_total; r0 += int64_t(gridDim.x) * C::ROWS) {
         const int64_t row = r0 + rl;
         const bool ok = row < rows_total;

@@ -155,6 +155,50 @@ inline cudaError_t launch_col_tma(Op op, const TW<Rl> *tw, int64_t nx, int64_t b
     return cudaGetLastError();
 }
 
+// PSS_TMA3=0 keeps the one-buffer tensor-copy column pass for ops that opted
+// into the three-buffer one (read per launch)
+inline bool tma3_enabled()
+{
+    const char *e = getenv("PSS_TMA3");
+    return !(e && e[0] == '0' && e[1] == 0);
+}
+
+// the three-buffer column pass: an op that opted in, two groups within the
+// per-SM thread budget the registers are planned for, three buffers within
+// the 227 KB of shared memory a CTA may have
+template <class Rl, int N, class Op> constexpr bool tma3_col()
+{
+    using C = ColCfgOf<Rl, N, Op, 0>;
+    return tma_col<Rl, N, Op>() && Tma3Op<Op>::value && 2 * C::THREADS <= PSS_THREADS_PER_SM &&
+           tma3_col_smem<C>() <= 227 * 1024;
+}
+
+template <class Rl, int N, class Op>
+inline cudaError_t launch_col_tma3(Op op, const TW<Rl> *tw, int64_t nx, int64_t batch, cudaStream_t s)
+{
+    using C = ColCfgOf<Rl, N, Op, 0>;
+    auto k = k_col_tma3<Rl, N, Op>;
+    constexpr size_t smem = tma3_col_smem<C>();
+    static std::atomic<unsigned> done{0};
+    static int ctas[32] = {};
+    cudaError_t e = allow_smem(k, smem, done);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = kept_groups(op, nx / C::W) * batch;
+    if (tiles <= 0) return cudaSuccess;
+    if (tiles > INT32_MAX - 2 * 65536) return cudaErrorInvalidValue;  // the kernel counts tiles in 32 bits
+    CUtensorMap map;
+    if ((e = encode_col_map(&map, op.in(0), int(sizeof(V2<Rl>)), in_stride(op, nx), N, batch, C::W)) != cudaSuccess)
+        return e;
+    int grid = 0;
+    if ((e = resident_ctas(k, 2 * C::THREADS, smem, ctas, &grid)) != cudaSuccess) return e;
+    if (tiles < grid) grid = int(tiles);
+    const char *f = getenv("PSS_FAULT");
+    const bool inject = f && strcmp(f, "tma_timeout") == 0;
+    k<<<dim3(unsigned(grid)), 2 * C::THREADS, smem, s>>>(map, op, tw, nx, batch, inject ? 64u : TMA_WAIT_LIMIT,
+                                                          inject ? 1 : 0);
+    return cudaGetLastError();
+}
+
 template <class Rl, int N, class Op>
 inline cudaError_t launch_row_n(Op op, const TW<Rl> *tw, int64_t rows_total, cudaStream_t s)
 {
@@ -174,6 +218,8 @@ inline cudaError_t launch_col_n(Op op, const TW<Rl> *tw, int64_t nx, int64_t bat
         if (nx % ColCfgOf<Rl, N, Op, 1>::W == 0 && plan_pick(slot) == 1)
             return launch_col_v<Rl, N, Op, 1>(op, tw, nx, batch, s);
     }
+    if constexpr (tma3_col<Rl, N, Op>())
+        if (tma_enabled() && tma3_enabled()) return launch_col_tma3<Rl, N, Op>(op, tw, nx, batch, s);
     if constexpr (tma_col<Rl, N, Op>())
         if (tma_enabled()) return launch_col_tma<Rl, N, Op>(op, tw, nx, batch, s);
     return launch_col_v<Rl, N, Op, 0>(op, tw, nx, batch, s);

@@ -131,6 +131,7 @@ template <class Rl, int VAR> struct VarShape {
     static constexpr int TPS = VAR == 1 ? 1024 : PSS_THREADS_PER_SM;
 };
 __host__ __device__ constexpr int imin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int imax(int a, int b) { return a > b ? a : b; }
 
 // dynamic shared memory a pass may use per CTA (the GB300 limit is 227 KB)
 constexpr size_t SMEM_LIMIT = 200 * 1024;
@@ -295,6 +296,8 @@ __global__ void __launch_bounds__(RowCfgOf<Rl, N, Op, VAR>::THREADS, RowCfgOf<Rl
     constexpr bool EARLY = EarlyNext<Op>::value && C::NBUF == 1;
     int64_t tile = blockIdx.x;
     if (C::NBUF == 2 || EARLY) issue(tile, 0);
+    fill_stage_tw<N, C::P>(tw);
+    __syncthreads();
     for (int it = 0; tile < tiles; ++it, tile += gridDim.x) {
         int b = 0;
         if constexpr (C::NBUF == 2) {
@@ -397,6 +400,8 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, VAR>::THREADS, ColCfgOf<Rl
 
     int64_t tile = blockIdx.x;
     if (C::NBUF == 2) issue(tile, 0);
+    fill_stage_tw<N, C::P>(tw);
+    __syncthreads();
     for (int it = 0; tile < tiles; ++it, tile += gridDim.x) {
         int b = 0;
         if constexpr (C::NBUF == 2) {
@@ -459,6 +464,7 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, 
     // 32-bit tile counters (the launcher checks the count): fewer live registers
     const int groups = int(kept_groups(op, nx / C::W)), tiles = groups * int(batch);
     if (threadIdx.x == 0) mbar_init(sbar, 1);
+    fill_stage_tw<N, C::P>(tw);
     __syncthreads();
     unsigned parity = 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, parity ^= 1u) {
@@ -482,6 +488,146 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, 
         const Sm sm[1] = {Sm{buf + c * C::STRIDE}};
         op.template col<N, C::P, C::BLOCK>(v, int64_t(field), x0 + c, t, sm, tw);
         fft_sync<C::BLOCK>();  // every read of this tile is done before the next copy lands
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Tensor-copy column pass with the copies one tile ahead.  With a single
+// staging buffer (k_col_tma) a CTA asks for its next tile only when it has
+// finished the current one, so every copy's latency is exposed to that CTA.
+// Here one CTA of two groups of C::THREADS threads (each group the shape of
+// one k_col_tma CTA) rotates three buffers: the CTA's k-th tile (blockIdx.x
+// + k gridDim.x) lands in buffer k mod 3 and is transformed by group k mod 2,
+// and a group that finishes tile k asks for tile k + 3 into the buffer it
+// has just released.  While both groups compute, the third buffer fills.
+// Each group synchronises on its own named barriers (fft_sync<THREADS>:
+// ids 1 and 2; the group votes below: ids 3 and 4), so the groups run
+// independently.  An op opts in with TMA3 = true (its exchanges must use
+// fft_sync<BLOCK>, not CTA-wide barriers).
+template <class Op, class = void> struct Tma3Op : std::false_type {};
+template <class Op>
+struct Tma3Op<Op, std::void_t<decltype(Op::TMA3)>> : std::integral_constant<bool, Op::TMA3> {};
+
+constexpr int TMA3_NBUF = 3;
+
+// dynamic shared memory: three buffers, room to align them to 128 bytes, an
+// mbarrier per buffer and the control words (abort flag, copies issued into
+// each buffer)
+template <class C> constexpr size_t tma3_col_smem()
+{
+    return TMA3_NBUF * C::SMEM + 128 + 8 * TMA3_NBUF + 4 * (1 + TMA3_NBUF);
+}
+
+// OR of `v` over the G threads of this thread's group (named barrier id)
+template <int G> __device__ __forceinline__ bool group_any(bool v, int id)
+{
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"(unsigned(v)), "r"(id), "n"(G)
+        : "memory");
+    return r != 0;
+}
+
+// mbar_wait that also gives up once the CTA's abort flag is set
+__device__ __forceinline__ bool mbar_wait_or_abort(unsigned bar, unsigned parity, unsigned limit,
+                                                   const volatile int *abort)
+{
+    for (unsigned i = 0; i < limit; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (*abort) return false;
+    }
+    return false;
+}
+
+template <class Rl, int N, class Op>
+__global__ void __launch_bounds__(2 * ColCfgOf<Rl, N, Op, 0>::THREADS,
+                                  imax(1, PSS_THREADS_PER_SM / (2 * ColCfgOf<Rl, N, Op, 0>::THREADS)))
+    k_col_tma3(const __grid_constant__ CUtensorMap map, Op op, const TW<Rl> *__restrict__ tw, int64_t nx,
+               int64_t batch, unsigned wait_limit, int skip_copy)
+{
+    using C = ColCfgOf<Rl, N, Op, 0>;
+    using V = V2<Rl>;
+    using Sm = SmemLine<V, C::PADLOG>;
+    constexpr int G = C::THREADS;  // threads per group
+    static_assert(C::NBUF == 1 && G % 32 == 0 && 2 * G <= 1024, "two groups of one-buffer tiles");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *const buf = reinterpret_cast<V *>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
+    const unsigned sbar = smem_addr(buf + TMA3_NBUF * C::BUF);  // mbarrier of buffer j at sbar + 8 j
+    volatile int *const ctrl = reinterpret_cast<volatile int *>(buf + TMA3_NBUF * C::BUF) + 2 * TMA3_NBUF;
+    const int grp = threadIdx.x / G, tg = threadIdx.x % G;
+    const int c = tg % C::W, t = tg / C::W;
+    const int groups = int(kept_groups(op, nx / C::W)), tiles = groups * int(batch);
+    const int stride = int(gridDim.x);
+
+    // one thread: ask for `tile` (this CTA's k-th, k = j mod 3) into buffer j
+    auto issue = [&](int tile, int j) {
+        if (tile >= tiles) return;
+        const int field = tile / groups;
+        const int x0 = int(group_index(op, tile - field * groups)) * C::W;
+        fence_proxy_async_smem();  // this buffer's earlier shared-memory accesses come first
+        mbar_arrive_expect_tx(sbar + 8 * j, unsigned(N * C::W * sizeof(V)));
+        // skip_copy (host fault injection only): announce the bytes but start
+        // no copy, so that the waits run out with nothing in flight
+        if (!skip_copy) tma_load_4d(smem_addr(buf + j * C::BUF), &map, sbar + 8 * j, 2 * x0, 0, 0, field);
+        ctrl[1 + j] = ctrl[1 + j] + 1;
+    };
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < TMA3_NBUF; ++j) {
+            mbar_init(sbar + 8 * j, 1);
+            ctrl[1 + j] = 0;
+        }
+        ctrl[0] = 0;
+        for (int j = 0; j < TMA3_NBUF; ++j) issue(int(blockIdx.x) + j * stride, j);
+    }
+    fill_stage_tw<N, C::P>(tw);
+    __syncthreads();
+
+    // the group's k-th tiles, k = grp, grp + 2, ...: buffer j = k mod 3, which
+    // the copy of use floor(k / 3) completes (phase parity `par`)
+    int j = grp, par = 0;
+    for (int tile = int(blockIdx.x) + grp * stride; tile < tiles; tile += 2 * stride) {
+        const bool landed = mbar_wait_or_abort(sbar + 8 * j, unsigned(par), wait_limit, ctrl);
+        if (group_any<G>(!landed, 3 + grp)) {
+            if (tg == 0) {
+                atomicOr(op.status, STATUS_TMA_TIMEOUT);
+                ctrl[0] = 1;  // the other group stops at its next wait
+                // leave no copy of this CTA in flight: wait (bounded) for the
+                // last copy issued into each buffer
+                for (int b = 0; b < TMA3_NBUF; ++b) {
+                    const int n = ctrl[1 + b];
+                    if (n > 0) mbar_wait(sbar + 8 * b, unsigned(n - 1) & 1u, wait_limit);
+                }
+            }
+            return;
+        }
+        V *const tb = buf + j * C::BUF;
+        const int field = tile / groups;
+        const int x0 = int(group_index(op, tile - field * groups)) * C::W;
+        V v[1][C::P];
+#pragma unroll
+        for (int m = 0; m < C::P; ++m) v[0][m] = tb[(t + C::T * m) * C::W + c];
+        const Sm sm[1] = {Sm{tb + c * C::STRIDE}};
+        op.template col<N, C::P, G>(v, int64_t(field), x0 + c, t, sm, tw);
+        fft_sync<G>();  // every access of this group to buffer j is done
+        if (tg == 0) issue(tile + TMA3_NBUF * stride, j);  // the CTA's (k + 3)-th tile, same buffer
+        j += 2;
+        if (j >= TMA3_NBUF) {
+            j -= TMA3_NBUF;
+            par ^= 1;
+        }
     }
 }
 

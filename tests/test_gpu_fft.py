@@ -5,7 +5,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import EPS, rel_l2
+from gpu_util import EPS, check
 
 pytestmark = pytest.mark.gpu
 
@@ -33,7 +33,7 @@ def test_fft2d_matches_oracle(lib, orc, cuda_device, precision, nx, ny, batch, d
     ref = np.stack([(orc.fft2d(x) if direction < 0 else orc.ifft2d(x)) for x in a])
     # error bound of a radix-r FFT grows like eps * log2(size)
     tol = 4 * EPS[precision] * math.log2(nx * ny)
-    assert rel_l2(got, ref) <= tol
+    check(got, ref, tol)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
@@ -53,7 +53,7 @@ def test_fft2d_round_trip_and_single_mode(lib, orc, cuda_device, precision):
     # zero outputs collect rounding from all nx*ny terms of magnitude 1
     assert np.abs(h - expect).max() <= 64 * EPS[precision] * math.log2(nx * ny) * nx * ny
     lib.pss_fft2d(t.data_ptr(), nx, ny, 1, prec, +1, s)
-    assert rel_l2(t.cpu().numpy()[0], mode) <= 8 * EPS[precision] * math.log2(nx * ny)
+    check(t.cpu().numpy()[0], mode, 8 * EPS[precision] * math.log2(nx * ny))
 
 
 def test_fft2d_rejects_bad_sizes(lib, cuda_device):

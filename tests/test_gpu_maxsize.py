@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synthetic as S
-from gpu_util import rel_l2
+from gpu_util import check
 
 pytestmark = pytest.mark.gpu
 
@@ -22,7 +22,7 @@ def test_nls_plane_wave_8192(lib, cuda_device, precision):
     g.step(steps)
     k2 = (2 * math.pi / L) ** 2 * 13
     exact = p0 * np.exp(-1j * (k2 + A * A) * dt * steps)
-    assert rel_l2(g.get_state()[0], exact) <= (1e-12 if precision == "fp64" else 1e-5)
+    check(g.get_state()[0], exact, 1e-12 if precision == "fp64" else 1e-5)
 
 
 def test_sg_uniform_field_8192_is_the_pendulum(lib, cuda_device):

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import synthetic as S
-from gpu_util import rel_l2
+from gpu_util import check
 
 pytestmark = pytest.mark.gpu
 
@@ -31,8 +31,7 @@ def test_config1_64_matches_oracle(lib, orc, cuda_device, precision):
     g.set_state(p0[None])
     g.step(steps)
     got = g.get_state()[0]
-    err = rel_l2(got, ref)
-    assert err <= (TOL64 if precision == "fp64" else TOL32_STATE), err
+    check(got, ref, TOL64 if precision == "fp64" else TOL32_STATE)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -50,10 +49,9 @@ def test_large_nonlinear_phase_plane_wave(lib, cuda_device, precision, phase):
     g.step(steps)
     k2 = (2 * math.pi / L) ** 2 * 13
     exact = p0 * np.exp(-1j * (k2 + sigma * A * A) * dt * steps)
-    err = rel_l2(g.get_state()[0], exact)
     # the phase itself is rounded once per step: 20 |th| eps relative
     eps = 2.2e-16 if precision == "fp64" else 1.2e-7
-    assert err <= 64 * steps * max(abs(phase), 1) * eps, err
+    check(g.get_state()[0], exact, 64 * steps * max(abs(phase), 1) * eps)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -67,8 +65,7 @@ def test_plane_wave_1024_closed_form(lib, cuda_device, precision):
     got = g.get_state()[0]
     k2 = (2 * math.pi / L) ** 2 * 13
     exact = p0 * np.exp(-1j * (k2 + A * A) * dt * steps)
-    err = rel_l2(got, exact)
-    assert err <= (1e-11 if precision == "fp64" else TOL32_STATE), err
+    check(got, exact, 1e-11 if precision == "fp64" else TOL32_STATE)
     m1, e1 = g.conserved()[0]
     # FP64: 4000 passes of ~1e-16 rounding each.  FP32: a single Fourier mode
     # rotates coherently, so the rounding errors of successive steps are
@@ -91,12 +88,10 @@ def test_config2_1024_matches_oracle_and_conserves_mass(lib, orc, cuda_device, p
     got = g.get_state()[0]
     (m1, e1), = g.conserved()
     rm, re_ = orc.nls_invariants(ref, L, L)
-    err = rel_l2(got, ref)
+    check(got, ref, TOL64 if precision == "fp64" else TOL32_STATE)
     if precision == "fp64":
-        assert err <= TOL64, err
         assert abs(m1 - rm) / rm <= 1e-12 and abs(e1 - re_) / abs(re_) <= 1e-9
     else:
-        assert err <= TOL32_STATE, err
         assert abs(m1 - m0) / m0 <= TOL32_MASS, (m1 - m0) / m0
 
 
@@ -141,7 +136,7 @@ def test_split_calls_equal_one_call(lib, cuda_device):
     b.step(15)
     b.step(0)
     b.step(25)
-    assert rel_l2(b.get_state(), a.get_state()) <= 1e-13
+    check(b.get_state(), a.get_state(), 1e-13)
 
 
 def test_non_square_grid_matches_oracle(lib, orc, cuda_device):
@@ -153,7 +148,7 @@ def test_non_square_grid_matches_oracle(lib, orc, cuda_device):
     g = lib.Grid("nls", (nx, ny), "fp64", lx=lx, ly=ly, dt=dt, sigma=-1.0)
     g.set_state(p0[None])
     g.step(steps)
-    assert rel_l2(g.get_state()[0], ref) <= TOL64
+    check(g.get_state()[0], ref, TOL64)
 
 
 def test_invariants_match_oracle(lib, orc, cuda_device):
@@ -192,6 +187,6 @@ def test_bench_configuration_fields_match_oracle(lib, orc, cuda_device):
     got = g.get_state()
     for i in (0, B - 1):
         ref = orc.nls_run(f[i], L, L, dt, steps, merged=True)
-        assert rel_l2(got[i], ref) <= TOL32_STATE
+        check(got[i], ref, TOL32_STATE)
     m1 = g.conserved()[:, 0]
     assert np.max(np.abs(m1 - m0) / m0) <= TOL32_MASS

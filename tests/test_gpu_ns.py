@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import synthetic as S
-from gpu_util import rel_l2
+from gpu_util import check
 
 pytestmark = pytest.mark.gpu
 
@@ -72,8 +72,7 @@ def test_random_field_matches_oracle(lib, orc, cuda_device, precision, n):
     g.set_state(w0[None])
     g.step(steps)
     got = g.get_state()[0]
-    err = rel_l2(got, orc.ns_field(ref))
-    assert err <= (TOL64 if precision == "fp64" else 1e-5), err
+    check(got, orc.ns_field(ref), TOL64 if precision == "fp64" else 1e-5)
     if precision == "fp64":
         assert g.stats()[1] == int(iters.sum())
     c0, z0, e0 = orc.ns_invariants(ref, L, L)
@@ -185,8 +184,7 @@ def test_midpoint_matches_oracle(lib, orc, cuda_device, precision, n):
     g = lib.Grid("ns", n, precision, lx=L, ly=L, dt=dt, nu=nu, tol=1e-10, dealias=1, scheme="midpoint")
     g.set_state(w0[None])
     g.step(steps)
-    err = rel_l2(g.get_state()[0], orc.ns_field(ref))
-    assert err <= (TOL64 if precision == "fp64" else 1e-5), err
+    check(g.get_state()[0], orc.ns_field(ref), TOL64 if precision == "fp64" else 1e-5)
     if precision == "fp64":
         assert g.stats()[1] == int(iters.sum())
 
@@ -256,8 +254,7 @@ def test_half_spectrum_matches_oracle(lib, orc, cuda_device, scheme, precision, 
     g = lib.Grid("ns", n, precision, lx=L, ly=L, dt=dt, nu=nu, tol=1e-10, dealias=1, scheme=scheme, rfft=1)
     g.set_state(w0[None])
     g.step(steps)
-    err = rel_l2(g.get_state()[0], orc.ns_field(ref))
-    assert err <= (TOL64 if precision == "fp64" else 1e-5), err
+    check(g.get_state()[0], orc.ns_field(ref), TOL64 if precision == "fp64" else 1e-5)
     if precision == "fp64":
         assert g.stats()[1] == int(iters.sum())
     c0, z0, e0 = orc.ns_invariants(ref, L, L)
@@ -290,7 +287,7 @@ def test_half_spectrum_non_square_and_without_dealiasing_matches_oracle(lib, orc
         g = lib.Grid("ns", (nx, ny), "fp64", lx=L, ly=L, dt=dt, nu=nu, dealias=dealias, rfft=1)
         g.set_state(w0[None])
         g.step(steps)
-        assert rel_l2(g.get_state()[0], orc.ns_field(ref)) <= TOL64
+        check(g.get_state()[0], orc.ns_field(ref), TOL64)
 
 
 def test_half_spectrum_batch_resume_graphs_and_fields(lib, cuda_device, monkeypatch):

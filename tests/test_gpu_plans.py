@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synthetic as S
-from gpu_util import rel_l2
+from gpu_util import check
 
 pytestmark = pytest.mark.gpu
 
@@ -24,7 +24,7 @@ def test_each_shape_matches_oracle_nls(lib, orc, cuda_device, monkeypatch, plan,
     g.set_state(p0[None])
     g.step(steps)
     ref = orc.nls_run(p0, L, L, dt, steps, merged=True)
-    assert rel_l2(g.get_state()[0], ref) <= 1e-5
+    check(g.get_state()[0], ref, 1e-5)
 
 
 @pytest.mark.parametrize("plan", ["0", "1"])
@@ -39,7 +39,7 @@ def test_each_shape_matches_oracle_sg(lib, orc, cuda_device, monkeypatch, plan, 
     g = lib.Grid("sg", n, "fp32", lx=Ls, ly=Ls, x0=-Ls / 2, y0=-Ls / 2, dt=dt, rfft=rfft)
     g.set_state(u0[None], v0[None])
     g.step(steps)
-    assert rel_l2(g.get_state()[0][0], ref) <= 2e-5
+    check(g.get_state()[0][0], ref, 2e-5)
 
 
 @pytest.mark.parametrize("eq", ["nls", "sg"])
@@ -78,14 +78,16 @@ def test_autotune_keeps_state_and_one_plan_per_key(lib, cuda_device, eq):
 
 @pytest.mark.parametrize("n", [256, 512, 1024, 2048, 4096])
 def test_tensor_copy_staging_is_bitwise_equal(lib, cuda_device, monkeypatch, n):
-    # The NLS column pass stages its tiles by one tensor copy each (PSS_TMA
-    # unset) or by per-point copies (PSS_TMA=0): the arithmetic is the same,
-    # so the states agree bit for bit, including a batch whose tiles wrap
-    # from one field to the next
+    # The NLS column pass stages its tiles by tensor copies into three
+    # rotating buffers (default), by one tensor copy into a single buffer
+    # (PSS_TMA3=0) or by per-point copies (PSS_TMA=0): the arithmetic is the
+    # same, so the states agree bit for bit, including a batch whose tiles
+    # wrap from one field to the next
     p0 = S.nls_gaussian(n, batch=3)
     out = []
-    for tma in ("1", "0"):
+    for tma, tma3 in (("1", "1"), ("1", "0"), ("0", "0")):
         monkeypatch.setenv("PSS_TMA", tma)
+        monkeypatch.setenv("PSS_TMA3", tma3)
         monkeypatch.setenv("PSS_PLAN", "0")
         g = lib.Grid("nls", n, "fp32", batch=3, lx=L, ly=L, x0=-L / 2, y0=-L / 2, dt=1e-3)
         g.set_state(p0)
@@ -94,6 +96,7 @@ def test_tensor_copy_staging_is_bitwise_equal(lib, cuda_device, monkeypatch, n):
         out.append(g.get_state())
         g.close()
     assert np.array_equal(out[0].view(np.uint32), out[1].view(np.uint32))
+    assert np.array_equal(out[0].view(np.uint32), out[2].view(np.uint32))
 
 
 @pytest.mark.parametrize("rfft", [0, 1])

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synthetic as S
-from gpu_util import rel_l2
+from gpu_util import check
 
 pytestmark = pytest.mark.gpu
 
@@ -21,7 +21,7 @@ def _check(results, reqs):
         ref = ref if isinstance(ref, tuple) else (ref,)
         for a, b in zip(got, ref):
             if q.eq == "nls":
-                assert rel_l2(a, b) <= 1e-5, (q.rid, rel_l2(a, b))
+                check(a, b, 1e-5)
             else:
                 assert np.array_equal(a, b), q.rid
 
@@ -66,7 +66,7 @@ def test_set_and_get_field_round_trip(lib, cuda_device):
         g.set_field(1, *state)
         out = g.get_field(1)
         a = out[0] if isinstance(out, tuple) else out
-        assert rel_l2(a, state[0]) <= 1e-13
+        check(a, state[0], 1e-13)
         # the other slots hold zeros
         z = g.get_field(0)
         z = z[0] if isinstance(z, tuple) else z

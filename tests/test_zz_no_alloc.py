@@ -38,27 +38,33 @@ def _device_fields(lib, g, precision, cuda_device):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_static_invariants_match_grid_entry_point_twice(lib, cuda_device, precision):
+def test_static_invariants_match_grid_entry_point_twice(lib, orc, cuda_device, precision):
     import torch
-    n = 256
-    expect, calls = [], []
-    for batch, seed in ((3, S.SEED_BASE), (2, S.SEED_BASE + 77)):
+    # two calls in a row that differ in grid size, batch and data: the first
+    # (256^2, 8 fields, amplitudes scaled by 3) fills more of the shared
+    # scratch than the second (16^2, 1 field) reads, so a partial sum the
+    # second call failed to rewrite, or read from the wrong place, would
+    # carry the first call's much larger values into its result
+    cases = ((256, 8, S.SEED_BASE, 3.0), (16, 1, S.SEED_BASE + 77, 1.0))
+    expect, calls, oracle_ref = [], [], []
+    for n, batch, seed, amp in cases:
+        fields = amp * S.nls_gaussian(n, seed=seed, batch=batch)
         g = lib.Grid("nls", n, precision, batch=batch, lx=L, ly=L, dt=1e-3)
-        g.set_state(S.nls_gaussian(n, seed=seed, batch=batch))
-        g.step(5)
+        g.set_state(fields)
         expect.append(g.conserved())  # existing entry point: mass, energy per field
         psi, hat, prec = _device_fields(lib, g, precision, cuda_device)
+        # the FP64 oracle on the same fields as the library holds them
+        oracle_ref.append(np.array([orc.nls_invariants(f, L, L) for f in psi.cpu().numpy()]))
         out = torch.full((2 * batch,), float("nan"), dtype=torch.float64, device=cuda_device)
         lib.pss_nls_invariants_static(psi.data_ptr(), hat.data_ptr(), n, n, batch, L, L, 1.0,
                                       prec, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
         calls.append(out.cpu().numpy().reshape(batch, 2))
         g.close()
-    # two calls in a row: the second (smaller batch, other data) must not
-    # reuse anything the first left in the shared scratch
-    for got, ref in zip(calls, expect):
+    for got, ref, orf in zip(calls, expect, oracle_ref):
         assert np.all(np.isfinite(got))
         assert np.max(np.abs(got - ref) / np.abs(ref)) <= TOL[precision]
+        assert np.max(np.abs(got - orf) / np.abs(orf)) <= TOL[precision]
 
 
 def test_static_invariants_reject_batch_beyond_scratch(lib, cuda_device):
