@@ -275,6 +275,10 @@ struct NoHook {
 #ifndef PSS_SMEM_TW
 #define PSS_SMEM_TW 1
 #endif
+// twiddle loads of the shared copy kept in flight per thread
+#ifndef PSS_TWD
+#define PSS_TWD 4
+#endif
 template <int N, int P> struct StageTw {
     using PL = Plan<N, P>;
     static constexpr bool ON = PSS_SMEM_TW && PL::STAGES >= 2;
@@ -337,7 +341,7 @@ __device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const 
                 static_assert(NS == StageTw<N, P>::NS && R == StageTw<N, P>::R, "stage 1 shape");
                 // TWD loads in flight, issued in order (volatile loads are not
                 // hoisted further, so at most TWD twiddles occupy registers)
-                constexpr int TWD = 4;
+                constexpr int TWD = PSS_TWD;
                 const unsigned a0 = smem_u32(stage_tw_smem<NS, R>()) + unsigned(jm) * 16u;
                 float4 ring[TWD];
 #pragma unroll

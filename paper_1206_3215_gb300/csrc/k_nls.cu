@@ -162,7 +162,7 @@ template <class Rl> struct NlsCol {
     static constexpr int NIN = 1;
     static constexpr bool LEAN = true;
     static constexpr int PMAX = 32;
-    static constexpr bool TMA3 = true;  // exchanges sync through fft_sync<BLOCK> only
+    static constexpr bool COL_LAND = true;  // exchanges sync through fft_sync<BLOCK> only
     V2<Rl> *data;
     int64_t nx;
     Rl scale;

@@ -155,30 +155,30 @@ inline cudaError_t launch_col_tma(Op op, const TW<Rl> *tw, int64_t nx, int64_t b
     return cudaGetLastError();
 }
 
-// PSS_TMA3=0 keeps the one-buffer tensor-copy column pass for ops that opted
-// into the three-buffer one (read per launch)
-inline bool tma3_enabled()
+// PSS_COL_LAND=0 keeps the one-buffer tensor-copy column pass for ops that
+// opted into the landing-buffer one (read per launch)
+inline bool land_enabled()
 {
-    const char *e = getenv("PSS_TMA3");
+    const char *e = getenv("PSS_COL_LAND");
     return !(e && e[0] == '0' && e[1] == 0);
 }
 
-// the three-buffer column pass: an op that opted in, two groups within the
-// per-SM thread budget the registers are planned for, three buffers within
-// the 227 KB of shared memory a CTA may have
-template <class Rl, int N, class Op> constexpr bool tma3_col()
+// the landing-buffer column pass: an op that opted in, two groups within the
+// per-SM thread budget the registers are planned for, the buffers and the
+// stage twiddles within the 227 KB of shared memory a CTA may have
+template <class Rl, int N, class Op> constexpr bool land_col()
 {
     using C = ColCfgOf<Rl, N, Op, 0>;
-    return tma_col<Rl, N, Op>() && Tma3Op<Op>::value && 2 * C::THREADS <= PSS_THREADS_PER_SM &&
-           tma3_col_smem<C>() <= 227 * 1024;
+    return tma_col<Rl, N, Op>() && LandOp<Op>::value && 2 * C::THREADS <= PSS_THREADS_PER_SM &&
+           land_col_smem<C>() + 16 * size_t(StageTw<N, C::P>::COUNT) <= 227 * 1024;
 }
 
 template <class Rl, int N, class Op>
-inline cudaError_t launch_col_tma3(Op op, const TW<Rl> *tw, int64_t nx, int64_t batch, cudaStream_t s)
+inline cudaError_t launch_col_land(Op op, const TW<Rl> *tw, int64_t nx, int64_t batch, cudaStream_t s)
 {
     using C = ColCfgOf<Rl, N, Op, 0>;
-    auto k = k_col_tma3<Rl, N, Op>;
-    constexpr size_t smem = tma3_col_smem<C>();
+    auto k = k_col_land<Rl, N, Op>;
+    constexpr size_t smem = land_col_smem<C>();
     static std::atomic<unsigned> done{0};
     static int ctas[32] = {};
     cudaError_t e = allow_smem(k, smem, done);
@@ -218,8 +218,8 @@ inline cudaError_t launch_col_n(Op op, const TW<Rl> *tw, int64_t nx, int64_t bat
         if (nx % ColCfgOf<Rl, N, Op, 1>::W == 0 && plan_pick(slot) == 1)
             return launch_col_v<Rl, N, Op, 1>(op, tw, nx, batch, s);
     }
-    if constexpr (tma3_col<Rl, N, Op>())
-        if (tma_enabled() && tma3_enabled()) return launch_col_tma3<Rl, N, Op>(op, tw, nx, batch, s);
+    if constexpr (land_col<Rl, N, Op>())
+        if (tma_enabled() && land_enabled()) return launch_col_land<Rl, N, Op>(op, tw, nx, batch, s);
     if constexpr (tma_col<Rl, N, Op>())
         if (tma_enabled()) return launch_col_tma<Rl, N, Op>(op, tw, nx, batch, s);
     return launch_col_v<Rl, N, Op, 0>(op, tw, nx, batch, s);

@@ -492,30 +492,32 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, 
 }
 
 // ----------------------------------------------------------------------------
-// Tensor-copy column pass with the copies one tile ahead.  With a single
+// Tensor-copy column pass whose copies overlap the transforms.  With one
 // staging buffer (k_col_tma) a CTA asks for its next tile only when it has
 // finished the current one, so every copy's latency is exposed to that CTA.
-// Here one CTA of two groups of C::THREADS threads (each group the shape of
-// one k_col_tma CTA) rotates three buffers: the CTA's k-th tile (blockIdx.x
-// + k gridDim.x) lands in buffer k mod 3 and is transformed by group k mod 2,
-// and a group that finishes tile k asks for tile k + 3 into the buffer it
-// has just released.  While both groups compute, the third buffer fills.
-// Each group synchronises on its own named barriers (fft_sync<THREADS>:
-// ids 1 and 2; the group votes below: ids 3 and 4), so the groups run
-// independently.  An op opts in with TMA3 = true (its exchanges must use
-// fft_sync<BLOCK>, not CTA-wide barriers).
-template <class Op, class = void> struct Tma3Op : std::false_type {};
+// Here a CTA holds two groups of C::THREADS threads (each the shape of one
+// k_col_tma CTA), each with its own exchange buffer, and one landing buffer
+// that the tiles arrive in (a dense [N][W] block).  The CTA's tiles k = 0, 1,
+// 2, ... (blockIdx.x + k gridDim.x) go to group k mod 2.  A group waits for
+// its tile in the landing buffer, reads it into registers and then at once
+// asks for the other group's next tile into the landing buffer, so that
+// copy lands while both groups compute; the transforms' exchanges use the
+// group's own buffer.  Copies for group g complete on mbarrier g (a
+// barrier's phases then follow one group's tiles, so their parities cannot
+// be confused).  Each group synchronises on its own named barriers
+// (fft_sync<THREADS>: ids 1 and 2; the votes below: ids 3 and 4), so the
+// groups run independently.  An op opts in with COL_LAND = true (its
+// exchanges must use fft_sync<BLOCK>, not CTA-wide barriers).
+template <class Op, class = void> struct LandOp : std::false_type {};
 template <class Op>
-struct Tma3Op<Op, std::void_t<decltype(Op::TMA3)>> : std::integral_constant<bool, Op::TMA3> {};
+struct LandOp<Op, std::void_t<decltype(Op::COL_LAND)>> : std::integral_constant<bool, Op::COL_LAND> {};
 
-constexpr int TMA3_NBUF = 3;
-
-// dynamic shared memory: three buffers, room to align them to 128 bytes, an
-// mbarrier per buffer and the control words (abort flag, copies issued into
-// each buffer)
-template <class C> constexpr size_t tma3_col_smem()
+// dynamic shared memory: two exchange buffers and the landing buffer, room to
+// align them to 128 bytes, two mbarriers and the control words (abort flag,
+// copies issued towards each group)
+template <class C> constexpr size_t land_col_smem()
 {
-    return TMA3_NBUF * C::SMEM + 128 + 8 * TMA3_NBUF + 4 * (1 + TMA3_NBUF);
+    return 2 * C::SMEM + size_t(C::T) * C::P * C::W * (C::SMEM / C::BUF) + 128 + 16 + 16;
 }
 
 // OR of `v` over the G threads of this thread's group (named barrier id)
@@ -533,9 +535,20 @@ template <int G> __device__ __forceinline__ bool group_any(bool v, int id)
     return r != 0;
 }
 
-// mbar_wait that also gives up once the CTA's abort flag is set
-__device__ __forceinline__ bool mbar_wait_or_abort(unsigned bar, unsigned parity, unsigned limit,
-                                                   const volatile int *abort)
+// volatile 32-bit shared-memory word access (control words of k_col_land)
+__device__ __forceinline__ int lds_vol(unsigned addr)
+{
+    int v;
+    asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts_vol(unsigned addr, int v)
+{
+    asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// mbar_wait that also gives up once the CTA's abort flag (at `abort`) is set
+__device__ __forceinline__ bool mbar_wait_or_abort(unsigned bar, unsigned parity, unsigned limit, unsigned abort)
 {
     for (unsigned i = 0; i < limit; ++i) {
         unsigned done;
@@ -547,7 +560,7 @@ __device__ __forceinline__ bool mbar_wait_or_abort(unsigned bar, unsigned parity
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
-        if (*abort) return false;
+        if (lds_vol(abort)) return false;
     }
     return false;
 }
@@ -555,7 +568,7 @@ __device__ __forceinline__ bool mbar_wait_or_abort(unsigned bar, unsigned parity
 template <class Rl, int N, class Op>
 __global__ void __launch_bounds__(2 * ColCfgOf<Rl, N, Op, 0>::THREADS,
                                   imax(1, PSS_THREADS_PER_SM / (2 * ColCfgOf<Rl, N, Op, 0>::THREADS)))
-    k_col_tma3(const __grid_constant__ CUtensorMap map, Op op, const TW<Rl> *__restrict__ tw, int64_t nx,
+    k_col_land(const __grid_constant__ CUtensorMap map, Op op, const TW<Rl> *__restrict__ tw, int64_t nx,
                int64_t batch, unsigned wait_limit, int skip_copy)
 {
     using C = ColCfgOf<Rl, N, Op, 0>;
@@ -564,70 +577,62 @@ __global__ void __launch_bounds__(2 * ColCfgOf<Rl, N, Op, 0>::THREADS,
     constexpr int G = C::THREADS;  // threads per group
     static_assert(C::NBUF == 1 && G % 32 == 0 && 2 * G <= 1024, "two groups of one-buffer tiles");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *const buf = reinterpret_cast<V *>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
-    const unsigned sbar = smem_addr(buf + TMA3_NBUF * C::BUF);  // mbarrier of buffer j at sbar + 8 j
-    volatile int *const ctrl = reinterpret_cast<volatile int *>(buf + TMA3_NBUF * C::BUF) + 2 * TMA3_NBUF;
+    V *const xbuf = reinterpret_cast<V *>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
+    V *const land = xbuf + 2 * C::BUF;                  // the dense [N][W] landing block
+    const unsigned sbar = smem_addr(land + N * C::W);   // mbarrier of group g at sbar + 8 g
+    const unsigned ctrl = sbar + 16;                    // [0] abort, [1 + g] copies issued towards group g
     const int grp = threadIdx.x / G, tg = threadIdx.x % G;
     const int c = tg % C::W, t = tg / C::W;
     const int groups = int(kept_groups(op, nx / C::W)), tiles = groups * int(batch);
-    const int stride = int(gridDim.x);
 
-    // one thread: ask for `tile` (this CTA's k-th, k = j mod 3) into buffer j
-    auto issue = [&](int tile, int j) {
+    // one thread: ask for `tile` into the landing buffer, for group g
+    auto issue = [&](int tile, int g) {
         if (tile >= tiles) return;
         const int field = tile / groups;
         const int x0 = int(group_index(op, tile - field * groups)) * C::W;
-        fence_proxy_async_smem();  // this buffer's earlier shared-memory accesses come first
-        mbar_arrive_expect_tx(sbar + 8 * j, unsigned(N * C::W * sizeof(V)));
+        fence_proxy_async_smem();  // the landing buffer's earlier reads come first
+        mbar_arrive_expect_tx(sbar + 8 * g, unsigned(N * C::W * sizeof(V)));
         // skip_copy (host fault injection only): announce the bytes but start
         // no copy, so that the waits run out with nothing in flight
-        if (!skip_copy) tma_load_4d(smem_addr(buf + j * C::BUF), &map, sbar + 8 * j, 2 * x0, 0, 0, field);
-        ctrl[1 + j] = ctrl[1 + j] + 1;
+        if (!skip_copy) tma_load_4d(smem_addr(land), &map, sbar + 8 * g, 2 * x0, 0, 0, field);
+        sts_vol(ctrl + 4 * (1 + g), lds_vol(ctrl + 4 * (1 + g)) + 1);
     };
     if (threadIdx.x == 0) {
-        for (int j = 0; j < TMA3_NBUF; ++j) {
-            mbar_init(sbar + 8 * j, 1);
-            ctrl[1 + j] = 0;
-        }
-        ctrl[0] = 0;
-        for (int j = 0; j < TMA3_NBUF; ++j) issue(int(blockIdx.x) + j * stride, j);
+        mbar_init(sbar, 1);
+        mbar_init(sbar + 8, 1);
+        sts_vol(ctrl, 0);
+        sts_vol(ctrl + 4, 0);
+        sts_vol(ctrl + 8, 0);
+        issue(int(blockIdx.x), 0);
     }
     fill_stage_tw<N, C::P>(tw);
     __syncthreads();
 
-    // the group's k-th tiles, k = grp, grp + 2, ...: buffer j = k mod 3, which
-    // the copy of use floor(k / 3) completes (phase parity `par`)
-    int j = grp, par = 0;
-    for (int tile = int(blockIdx.x) + grp * stride; tile < tiles; tile += 2 * stride) {
-        const bool landed = mbar_wait_or_abort(sbar + 8 * j, unsigned(par), wait_limit, ctrl);
+    const Sm sm[1] = {Sm{xbuf + grp * C::BUF + c * C::STRIDE}};
+    unsigned par = 0;
+    for (int tile = int(blockIdx.x) + grp * int(gridDim.x); tile < tiles; tile += 2 * int(gridDim.x), par ^= 1u) {
+        const bool landed = mbar_wait_or_abort(sbar + 8 * grp, par, wait_limit, ctrl);
         if (group_any<G>(!landed, 3 + grp)) {
             if (tg == 0) {
                 atomicOr(op.status, STATUS_TMA_TIMEOUT);
-                ctrl[0] = 1;  // the other group stops at its next wait
+                sts_vol(ctrl, 1);  // the other group stops at its next wait
                 // leave no copy of this CTA in flight: wait (bounded) for the
-                // last copy issued into each buffer
-                for (int b = 0; b < TMA3_NBUF; ++b) {
-                    const int n = ctrl[1 + b];
-                    if (n > 0) mbar_wait(sbar + 8 * b, unsigned(n - 1) & 1u, wait_limit);
+                // last copy issued towards each group
+                for (int g = 0; g < 2; ++g) {
+                    const int n = lds_vol(ctrl + 4 * (1 + g));
+                    if (n > 0) mbar_wait(sbar + 8 * g, unsigned(n - 1) & 1u, wait_limit);
                 }
             }
             return;
         }
-        V *const tb = buf + j * C::BUF;
-        const int field = tile / groups;
-        const int x0 = int(group_index(op, tile - field * groups)) * C::W;
         V v[1][C::P];
 #pragma unroll
-        for (int m = 0; m < C::P; ++m) v[0][m] = tb[(t + C::T * m) * C::W + c];
-        const Sm sm[1] = {Sm{tb + c * C::STRIDE}};
+        for (int m = 0; m < C::P; ++m) v[0][m] = land[(t + C::T * m) * C::W + c];
+        fft_sync<G>();  // the group has read the landing buffer: refill it for the other group
+        if (tg == 0) issue(tile + int(gridDim.x), grp ^ 1);
+        const int field = tile / groups;
+        const int x0 = int(group_index(op, tile - field * groups)) * C::W;
         op.template col<N, C::P, G>(v, int64_t(field), x0 + c, t, sm, tw);
-        fft_sync<G>();  // every access of this group to buffer j is done
-        if (tg == 0) issue(tile + TMA3_NBUF * stride, j);  // the CTA's (k + 3)-th tile, same buffer
-        j += 2;
-        if (j >= TMA3_NBUF) {
-            j -= TMA3_NBUF;
-            par ^= 1;
-        }
     }
 }
 

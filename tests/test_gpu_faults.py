@@ -40,18 +40,18 @@ def test_forced_non_convergence(lib, cuda_device, monkeypatch):
     g.close()
 
 
-@pytest.mark.parametrize("tma3", ["1", "0"])
+@pytest.mark.parametrize("land", ["1", "0"])
 @pytest.mark.parametrize("n", [256, 1024])
-def test_lost_tile_copy_is_reported_and_handle_recovers(lib, cuda_device, monkeypatch, n, tma3):
+def test_lost_tile_copy_is_reported_and_handle_recovers(lib, cuda_device, monkeypatch, n, land):
     # the column pass's tile copies never arrive: every CTA's bounded wait runs
     # out, it sets the grid's status word and returns; the next synchronising
     # call reports the state as lost, and the handle steps again once the
     # state is set again (the captured step graphs are rebuilt).  Both the
-    # three-buffer pass (a group that gives up stops the other group and
-    # waits, bounded, for the copies it issued) and the one-buffer pass
+    # landing-buffer pass (a group that gives up stops the other group and
+    # waits, bounded, for the copies issued) and the one-buffer pass
     p0 = S.nls_gaussian(n, batch=2)
     monkeypatch.setenv("PSS_PLAN", "0")
-    monkeypatch.setenv("PSS_TMA3", tma3)
+    monkeypatch.setenv("PSS_COL_LAND", land)
     monkeypatch.setenv("PSS_FAULT", "tma_timeout")
     g = lib.Grid("nls", n, "fp32", batch=2, lx=L, ly=L, x0=-L / 2, y0=-L / 2, dt=1e-3)
     g.set_state(p0)

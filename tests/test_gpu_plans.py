@@ -78,16 +78,16 @@ def test_autotune_keeps_state_and_one_plan_per_key(lib, cuda_device, eq):
 
 @pytest.mark.parametrize("n", [256, 512, 1024, 2048, 4096])
 def test_tensor_copy_staging_is_bitwise_equal(lib, cuda_device, monkeypatch, n):
-    # The NLS column pass stages its tiles by tensor copies into three
-    # rotating buffers (default), by one tensor copy into a single buffer
-    # (PSS_TMA3=0) or by per-point copies (PSS_TMA=0): the arithmetic is the
+    # The NLS column pass stages its tiles by tensor copies into a landing
+    # buffer shared by two groups (default), by one tensor copy into a single
+    # buffer (PSS_COL_LAND=0) or by per-point copies (PSS_TMA=0): the arithmetic is the
     # same, so the states agree bit for bit, including a batch whose tiles
     # wrap from one field to the next
     p0 = S.nls_gaussian(n, batch=3)
     out = []
-    for tma, tma3 in (("1", "1"), ("1", "0"), ("0", "0")):
+    for tma, land in (("1", "1"), ("1", "0"), ("0", "0")):
         monkeypatch.setenv("PSS_TMA", tma)
-        monkeypatch.setenv("PSS_TMA3", tma3)
+        monkeypatch.setenv("PSS_COL_LAND", land)
         monkeypatch.setenv("PSS_PLAN", "0")
         g = lib.Grid("nls", n, "fp32", batch=3, lx=L, ly=L, x0=-L / 2, y0=-L / 2, dt=1e-3)
         g.set_state(p0)
