@@ -37,7 +37,7 @@ UNIT = "Gpt-steps/s"
 N = 1024
 L = 20 * math.pi
 DT = 1e-3
-FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate (no measured FP64 peak is available)
+FP64_NOMINAL_GFLOPS = 1250.0  # nominal GB300 FP64 rate, used only if the measurement fails
 E2E_STEPS = 2000  # one full solve of the 1024^2 configuration per e2e iteration
 
 
@@ -60,7 +60,10 @@ def parse():
     ap.add_argument("--only", default=None, help="with --other-only: just this line (e.g. sg_2048_fp32_half)")
     ap.add_argument("--paper-tables", action="store_true",
                     help="replay the runs of Tables 2-4 instead (one JSON line with both timings)")
-    ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=60.0, help="mean arrivals per second")
+    ap.add_argument("--repeats", type=int, default=5, help="extra timed regions of K steps (median reported)")
+    ap.add_argument("--no-plane-wave", action="store_true")
     return ap.parse_args()
 
 
@@ -75,6 +78,8 @@ def dist_env():
 # clocks during the timed region
 
 class ClockSampler:
+    """nvidia-smi samples (every 50 ms) with their host time, so that a
+    window (the timed regions) can be summarised on its own."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -82,7 +87,7 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.lines: list[str] = []
+        self.lines: list = []  # (host time, csv line)
 
     def __enter__(self):
         try:
@@ -98,7 +103,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def __exit__(self, *a):
         if self.proc:
@@ -108,10 +113,14 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, windows=None):
+        """Median SM clock and the throttle reasons seen, over all samples or
+        over those inside the given (start, end) host-time windows."""
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for t, ln in self.lines:
+            if windows is not None and not any(a <= t <= b for a, b in windows):
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -124,7 +133,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(nm)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
 
@@ -164,8 +173,9 @@ NLS_KERNEL_FILES = ("fft_core.cuh", "passes.cuh", "launch.cuh", "tma.cuh", "tma.
 
 
 # the kernels the roofline reports, by pass (launch shape 0; the column pass of
-# that shape stages its tiles by tensor copies); keys of profiles/traffic.json
-ROOFLINE_KERNELS = {"col": "k_col_tma<float, 1024, NlsCol<float>>", "row": "k_row<float, 1024, NlsRow<float>, 0>"}
+# that shape stages its tiles by tensor copies into a landing buffer shared by
+# two groups); keys of profiles/traffic.json
+ROOFLINE_KERNELS = {"col": "k_col_land<float, 1024, NlsCol<float>>", "row": "k_row<float, 1024, NlsRow<float>, 0>"}
 
 
 def kernel_source_hash(files=NLS_KERNEL_FILES) -> str:
@@ -422,6 +432,10 @@ def run_ours(args):
     plans_changed = 0 if args.no_autotune else g.autotune(4)
     mass0 = g.conserved()[:, 0].copy()
 
+    # clocks are sampled from here to the end of the GPU work (the timed
+    # region alone can be a few milliseconds: too short for the sampler)
+    clk = ClockSampler(local).__enter__()
+
     # warm-up
     g.step(args.warmup)
     g.sync()
@@ -431,22 +445,41 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    # timed region: K steps through the library, device-resident state
+    # timed region: K steps through the library, device-resident state; the
+    # library records an event pair around every pass (per-pass times for the
+    # roofline, on the library's stream)
     P.pss_set_profiling(g.h, True)
-    with ClockSampler(local) as clk:
-        barrier()
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        g.step(args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        barrier()
+    barrier()
+    torch.cuda.synchronize(dev)
+    t_timed = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
     ms = reduce_max(e0.elapsed_time(e1), dev)
     prof = P.pss_profile_read(g.h)
     P.pss_set_profiling(g.h, False)
+    # the same K steps timed again `repeats` times, as the step graphs run them
+    # (no per-pass events): median, min and max
+    reps = []
+    for _ in range(args.repeats):
+        torch.cuda.synchronize(dev)
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        g.step(args.steps)
+        r1.record(stream)
+        torch.cuda.synchronize(dev)
+        reps.append(reduce_max(r0.elapsed_time(r1), dev))
+    timed_window = (t_timed - 0.05, time.perf_counter() + 0.05)
+    repeats = None
+    if reps:
+        rates = sorted(whole_job_rate(B * n * n * args.steps, world, r / 1e3) / 1e9 for r in reps)
+        repeats = {"n": len(reps), "steps_each": args.steps, "graphs": True, "unit": UNIT,
+                   "median": statistics.median(rates), "min": rates[0], "max": rates[-1]}
     mass1 = g.conserved()[:, 0]
-    total_steps = args.warmup + args.steps
+    total_steps = args.warmup + args.steps * (1 + args.repeats)
     drift = float(np.max(np.abs(mass1 - mass0) / mass0))
 
     value = whole_job_rate(B * n * n * args.steps, world, ms / 1e3) / 1e9
@@ -473,6 +506,14 @@ def run_ours(args):
                 # whole step (row + column pass) against the same peak
                 "step_frac": 2 * bytes_per_pass / (ms / args.steps / 1e3) / 1e9 / hbm}
 
+    # FMA-chain rates of this GPU (the ALU peaks): FP32, FP64, FP32 packed pairs
+    alu_peaks = {}
+    for kind, key in ((0, "fp32_fma_gflops"), (1, "fp64_fma_gflops"), (2, "fp32x2_fma_gflops")):
+        try:
+            alu_peaks[key] = P.pss_fma_rate(kind, stream.cuda_stream)
+        except Exception as ex:  # the roofline then says "nominal"
+            alu_peaks[key + "_error"] = str(ex)
+
     # FP64 path on the same workload (fewer steps; it is ALU bound on GB300)
     fp64 = None
     if not args.no_fp64:
@@ -494,9 +535,11 @@ def run_ours(args):
         # step (pointwise work not counted), against the nominal FP64 rate
         flops_pt = 2 * 5 * 2 * math.log2(n)
         achieved64 = v64 / world * flops_pt  # GFLOP/s per GPU
+        peak64 = alu_peaks.get("fp64_fma_gflops") or FP64_NOMINAL_GFLOPS
+        kind64 = "measured (pss_fma_rate, FP64 FMA chains)" if alu_peaks.get("fp64_fma_gflops") else "nominal"
         fp64 = {"value": v64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
-                "roofline": {"bound": "alu", "achieved": achieved64, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                             "frac": achieved64 / FP64_PEAK_GFLOPS, "peak_kind": "nominal",
+                "roofline": {"bound": "alu", "achieved": achieved64, "peak": peak64, "unit": "GFLOP/s",
+                             "frac": achieved64 / peak64, "peak_kind": kind64,
                              "flops_per_point_step": flops_pt,
                              "convention": "5 N log2 N per complex transform, 2D forward + inverse per step"}}
         g64.close()
@@ -533,21 +576,47 @@ def run_ours(args):
                              "seconds": te / iters, "mass_drift_max_rel": drift2000}}
         ge.close()
 
+    # FP32 mass drift of the single-mode plane wave (A = 0.5, mode (3, 2), 1024^2):
+    # the whole mass sits in one Fourier coefficient, whose rounding is not
+    # averaged over the field, so the drift is a random walk of about one
+    # FP32 rounding per step (sign changes, growth ~ sqrt(steps))
+    plane = None
+    if not args.no_plane_wave:
+        gp = P.Grid("nls", n, "fp32", batch=1, lx=L, ly=L, x0=-L / 2, y0=-L / 2, dt=DT, stream=stream.cuda_stream)
+        gp.set_state(S.nls_plane_wave(n, A=0.5, m=(3, 2))[None])
+        pm0 = float(gp.conserved()[0, 0])
+        traj, done = [], 0
+        for target in (500, 1000, 2000, 4000):
+            gp.step(target - done)
+            done = target
+            traj.append([target, float((gp.conserved()[0, 0] - pm0) / pm0)])
+        gp.close()
+        d2000 = abs(dict((k, v) for k, v in traj)[2000])
+        plane = {"mass_drift_rel_at_steps": traj, "steps": 2000, "mass_drift_rel": d2000, "target": 1e-6,
+                 "target_met": d2000 <= 1e-6,
+                 "note": "single Fourier mode: FP32 rounding of its coefficient is not averaged over the field; "
+                         "the drift is a random walk (sign changes, ~sqrt(steps)), not a bias"}
+
     # served latency: a seeded Poisson stream of mixed NLS / SG / NS solves
     # (N in 128..2048, 50-500 steps, FP32) through the continuous-batching server
     serve = None
     if not args.no_serve:
         from paper_1206_3215_gb300.serving import Request, Server
-        mix = [Request.from_dict(d) for d in S.serving_mix(args.serve_requests, 40.0, seed=S.SEED_BASE + 4 + rank)]
+        mix = [Request.from_dict(d) for d in S.serving_mix(args.serve_requests, args.serve_rate,
+                                                            seed=S.SEED_BASE + 4 + rank, fields_per_shape=4)]
         srv = Server(slots=8, round_max=50)
-        _, st = srv.run(mix, realtime=True, timeout=300)
+        _, st = srv.run(mix, realtime=True, timeout=900)
         srv.close()
-        serve = {"requests": st["requests"], "arrival_rate_hz": 40.0, "p50_latency_ms": st["p50_latency_s"] * 1e3,
-                 "p99_latency_ms": st["p99_latency_s"] * 1e3, "throughput_gpt_steps_s": st["gpt_steps_per_s"],
+        serve = {"requests": st["requests"], "arrival_rate_hz": args.serve_rate,
+                 "p50_latency_ms": st["p50_latency_s"] * 1e3, "p99_latency_ms": st["p99_latency_s"] * 1e3,
+                 "mean_queue_ms": st["mean_queue_s"] * 1e3, "throughput_gpt_steps_s": st["gpt_steps_per_s"],
+                 "throughput_requests_s": st["requests"] / st["wall_s"],
                  "wall_s": st["wall_s"], "pools": st["pools"], "rounds": st["rounds"],
-                 "mix": "NLS/SG/NS FP32, N in {128,256,512,1024,2048}, 50-500 steps, min(8, 2^22/N^2) slots per pool"}
+                 "mix": "seeded Poisson arrivals; NLS/SG/NS FP32, N in {128,256,512,1024,2048}, 50-500 steps, "
+                        "4 seeded fields per (equation, N); min(8, 2^22/N^2) slots per pool"}
 
     other = None if args.no_other else other_paths(stream, rank, autotune=not args.no_autotune)
+    clk.__exit__(None, None, None)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -562,7 +631,10 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32)", "data": "synthetic",
             "config": workload_config(n, B, world),
-            "accuracy": {"mass_drift_max_rel": drift, "steps_run": total_steps},
+            "accuracy": {"mass_drift_max_rel": drift, "steps_run": total_steps, "mass_drift_target": 1e-6,
+                         "target_met": drift <= 1e-6, "plane_wave": plane},
+            "repeats": repeats,
+            "alu_peaks": alu_peaks,
             "plans_changed_by_autotune": plans_changed,
             "fp64": fp64,
             "roofline": roofline,
@@ -571,7 +643,12 @@ def run_ours(args):
             "serving": serve,
             "other_paths": other,
             "gpu_launches": prof["launches"],
-            "clocks": clk.summary(),
+            # samples inside the timed regions (the K steps and their repeats);
+            # if that window is shorter than the 50 ms sampling period, every
+            # sample from the warm-up to the end of the GPU work
+            "clocks": (lambda a, b: dict(a, window="timed regions") if a["samples"] else
+                       dict(b, window="warm-up to the end of the GPU work"))(clk.summary([timed_window]),
+                                                                                 clk.summary()),
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -261,6 +261,15 @@ int pss_nls_invariants_static(const void *psi, const void *psi_hat, int64_t nx, 
                               int64_t batch, double lx, double ly, double sigma, int precision,
                               double *out, void *stream);
 
+/* Fused multiply-add rate of the current device in GFLOP/s (2 flops per FMA),
+ * the peak that arithmetic-bound passes are compared with.  The paper has no
+ * counterpart.  kind 0: FP32 FMA; 1: FP64 FMA; 2: FP32 FMA on packed pairs
+ * (two FMAs per instruction).  One launch of independent FMA chains (8 CTAs
+ * of 256 threads per SM), timed with CUDA events on `stream` (NULL: the
+ * legacy default stream), best of three after a warm-up; synchronises the
+ * stream.  Allocates nothing.  Errors: PSS_E_ARG, PSS_E_CUDA. */
+int pss_fma_rate(int kind, double *gflops, void *stream);
+
 /* Library version string. */
 const char *pss_version(void);
 

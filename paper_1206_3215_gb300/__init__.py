@@ -29,6 +29,7 @@ EXPORTED = [
     "pss_checkpoint_load", "pss_sync", "pss_destroy", "pss_last_error", "pss_fft2d",
     "pss_version", "pss_set_profiling", "pss_profile_read", "pss_nls_invariants_static",
     "pss_set_field", "pss_get_field", "pss_set_state_sg_levels", "pss_step_n_batch", "pss_autotune",
+    "pss_fma_rate",
 ]
 
 
@@ -78,6 +79,7 @@ def load_library(path: str = LIB_PATH):
             "pss_checkpoint_save": (I, [P, P, I]),
             "pss_checkpoint_load": (I, [P, P, I]),
             "pss_sync": (I, [P]),
+            "pss_fma_rate": (I, [I, P, P]),
             "pss_destroy": (I, [P]),
             "pss_last_error": (ctypes.c_char_p, [P]),
             "pss_fft2d": (I, [P, I64, I64, I64, I, I, P]),
@@ -227,6 +229,13 @@ def pss_nls_invariants_static(psi_ptr: int, hat_ptr: int, nx: int, ny: int, batc
     """NLS mass and energy into a device array, with no allocation (see pss.h)."""
     _check(load_library().pss_nls_invariants_static(psi_ptr, hat_ptr, nx, ny, batch, lx, ly, sigma,
                                                      precision, out_ptr, stream), None)
+
+
+def pss_fma_rate(kind: int, stream: int | None = None) -> float:
+    """GFLOP/s of independent FMA chains: kind 0 FP32, 1 FP64, 2 FP32 packed pairs."""
+    out = ctypes.c_double()
+    _check(load_library().pss_fma_rate(kind, ctypes.byref(out), stream))
+    return out.value
 
 
 def pss_version() -> str:

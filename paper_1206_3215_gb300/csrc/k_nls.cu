@@ -158,10 +158,60 @@ template <class V, class W> __device__ __forceinline__ V apply_km1(V z, W km1)
     return cadd(z, twmul<-1>(z, km1));
 }
 
+// s z + z (s (K - 1)) for a power of two s, given skm1 = s (K - 1) (hi + lo):
+// the increment is formed as in apply_km1 and s z (exact) is added inside
+// the last fused multiply-add, so the result is bitwise that of
+// apply_km1(s z, K - 1) with the scaling folded in (two instructions fewer)
+__device__ __forceinline__ float2 apply_skm1(float2 z, float s, float4 skm1)
+{
+    const float cr = __fmaf_rn(z.x, skm1.z, -z.y * skm1.w);
+    const float ci = __fmaf_rn(z.x, skm1.w, z.y * skm1.z);
+    const float ir = __fmaf_rn(z.x, skm1.x, __fmaf_rn(-z.y, skm1.y, cr));
+    const float ii = __fmaf_rn(z.x, skm1.y, __fmaf_rn(z.y, skm1.x, ci));
+    return {__fmaf_rn(z.x, s, ir), __fmaf_rn(z.y, s, ii)};
+}
+
+// row factors of the propagator kept in flight per thread (FP32 column pass)
+#ifndef PSS_KD
+#define PSS_KD 4
+#endif
+
+// a 16-byte read-only global load kept in program order
+__device__ __forceinline__ float4 ldg_nc_f4(const float4 *p)
+{
+    float4 r;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p));
+    return r;
+}
+
+// The FP32 column pass at n = 1024 keeps the row factors exp(-i ky^2 tau) - 1
+// in shared memory: only n/2 + 1 distinct values (ky^2 is even in ky), 8 KB,
+// which fits beside every column kernel's buffers without lowering its
+// occupancy.  The landing-buffer pass leaves the L1 cache too little room to
+// keep the 16 KB table, whose loads then wait on L2.  At other lengths the
+// factors are read from the global table.
+__host__ __device__ constexpr bool nls_ky_smem(int n) { return n == 1024; }
+template <int NH> __device__ __forceinline__ float4 *nls_ky_cache()
+{
+    __shared__ __align__(16) float4 cache[NH];
+    return cache;
+}
+
 template <class Rl> struct NlsCol {
     static constexpr int NIN = 1;
     static constexpr bool LEAN = true;
     static constexpr int PMAX = 32;
+    // all threads of the CTA, before the first tile: the row factors of
+    // ky index 0 .. n/2 into shared memory (the kernel synchronises after)
+    template <int N> __device__ __forceinline__ void prologue() const
+    {
+        if constexpr (sizeof(Rl) == 4 && nls_ky_smem(N)) {
+            float4 *c = nls_ky_cache<N / 2 + 1>();
+            for (int i = int(threadIdx.x); i <= N / 2; i += int(blockDim.x)) c[i] = __ldg(by + i);
+        }
+    }
     static constexpr bool COL_LAND = true;  // exchanges sync through fft_sync<BLOCK> only
     V2<Rl> *data;
     int64_t nx;
@@ -180,11 +230,48 @@ template <class Rl> struct NlsCol {
         auto propagate = [&]() {
             const TW<Rl> a = __ldg(ax + x);
             const TW<Rl> *byl = launder(by);  // keep these loads after the transform
+            if constexpr (sizeof(Rl) == 4) {
+                // scale is a power of two: s (Kx - 1) is exact
+                const float4 sa{a.x * scale, a.y * scale, a.z * scale, a.w * scale};
+                // the row factors by[t + T m]: KD loads in flight, issued in
+                // order ahead of their use (volatile loads are not hoisted
+                // further, so at most KD factors occupy registers)
+                constexpr int KD = PSS_KD;
+                float4 ring[KD];
+                if constexpr (nls_ky_smem(N)) {
+                    // element y = t + T m of the table, folded to min(y, N - y)
+                    const unsigned lo = smem_u32(nls_ky_cache<N / 2 + 1>()) + 16u * unsigned(t);
+                    const unsigned hi = smem_u32(nls_ky_cache<N / 2 + 1>()) + 16u * unsigned(N - t);
+                    auto ky = [&](int m) {
+                        return T * m <= N / 2 - T ? lds_f4(lo + 16u * unsigned(T * m))
+                                                  : lds_f4(hi - 16u * unsigned(T * m));
+                    };
 #pragma unroll
-            for (int m = 0; m < P; ++m) {
-                // scale is a power of two: exact
-                const V2<Rl> z = apply_km1(cscale(v[m], scale), a);
-                v[m] = apply_km1(z, __ldg(byl + t + T * m));
+                    for (int m = 0; m < KD && m < P; ++m) ring[m] = ky(m);
+#pragma unroll
+                    for (int m = 0; m < P; ++m) {
+                        const float4 b = ring[m % KD];
+                        if (m + KD < P) ring[m % KD] = ky(m + KD);
+                        v[m] = apply_km1(apply_skm1(v[m], scale, sa), b);
+                    }
+                } else {
+                    const float4 *bp = byl + t;
+#pragma unroll
+                    for (int m = 0; m < KD && m < P; ++m) ring[m] = ldg_nc_f4(bp + T * m);
+#pragma unroll
+                    for (int m = 0; m < P; ++m) {
+                        const float4 b = ring[m % KD];
+                        if (m + KD < P) ring[m % KD] = ldg_nc_f4(bp + T * (m + KD));
+                        v[m] = apply_km1(apply_skm1(v[m], scale, sa), b);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < P; ++m) {
+                    // scale is a power of two: exact
+                    const V2<Rl> z = apply_km1(cscale(v[m], scale), a);
+                    v[m] = apply_km1(z, __ldg(byl + t + T * m));
+                }
             }
         };
         if constexpr (PSS_SHARED_FFT && sizeof(Rl) == 4) {

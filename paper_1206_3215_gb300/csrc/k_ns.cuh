@@ -131,6 +131,7 @@ template <class Rl> struct NsRow {
 // two on twice as many columns.
 template <class Rl, bool MID, bool HALF = false> struct NsCol {
     static constexpr int NIN = 1;
+    static constexpr bool COL_LAND = true;  // exchanges and the norm partial sync per tile (BLOCK)
     static constexpr bool LEAN = NS_LEAN;
     static constexpr int PMAX = NS_PMAX;
     static constexpr int NOUT = HALF ? 4 : 2;  // inverse transforms per column
@@ -272,22 +273,36 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
         }
         // FP64 partial of |w^{k+1} - w^k|^2 over this tile, folded in a fixed order
         const int64_t g = x / W;
-        block_partial(acc, partials + field * (nx / W - skip_n) + (g < skip_lo ? g : g - skip_n));
+        block_partial<BLOCK>(acc, partials + field * (nx / W - skip_n) + (g < skip_lo ? g : g - skip_n));
     }
-    // sum over the CTA (all threads of the tile) in a fixed tree; thread 0 writes
-    __device__ __forceinline__ void block_partial(double acc, double *out) const
+    // sum over the threads of the tile in a fixed tree; the tile's first
+    // thread writes.  BLOCK <= 1: the tile is the CTA; BLOCK > 1: a group of
+    // BLOCK threads of a CTA that holds two tiles (its own named barrier, its
+    // own warps' slots)
+    template <int BLOCK> __device__ __forceinline__ void block_partial(double acc, double *out) const
     {
         __shared__ double red[32];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        __syncthreads();
-        if (lane == 0) red[warp] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int i = 0; i < int((blockDim.x + 31) >> 5); ++i) s += red[i];
-            *out = s;
+        if constexpr (BLOCK > 1) {
+            fft_sync<BLOCK>();
+            if (lane == 0) red[warp] = acc;
+            fft_sync<BLOCK>();
+            if (threadIdx.x % BLOCK == 0) {
+                double s = 0.0;
+                for (int i = 0; i < BLOCK / 32; ++i) s += red[warp + i];
+                *out = s;
+            }
+        } else {
+            __syncthreads();
+            if (lane == 0) red[warp] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double s = 0.0;
+                for (int i = 0; i < int((blockDim.x + 31) >> 5); ++i) s += red[i];
+                *out = s;
+            }
         }
     }
 };

@@ -262,6 +262,18 @@ __device__ __forceinline__ void read_line(V (&v)[P], const Sm &sm, int t)
 // ----------------------------------------------------------------------------
 // Kernel shells
 
+// An op may define prologue<N>(): work every thread of a CTA does once before
+// the first tile (filling shared-memory tables); the kernel synchronises
+// after it.
+template <class Op, class = void> struct HasPrologue : std::false_type {};
+template <class Op>
+struct HasPrologue<Op, std::void_t<decltype(std::declval<const Op &>().template prologue<1024>())>>
+    : std::true_type {};
+template <int N, class Op> __device__ __forceinline__ void op_prologue(const Op &op)
+{
+    if constexpr (HasPrologue<Op>::value) op.template prologue<N>();
+}
+
 // An op that sets EARLY_NEXT takes a hook as the last argument of row() and
 // calls it once its last transform has made its last shared-memory access
 // (block_fft's hook): a single-buffered row pass then issues the copies of
@@ -297,6 +309,7 @@ __global__ void __launch_bounds__(RowCfgOf<Rl, N, Op, VAR>::THREADS, RowCfgOf<Rl
     int64_t tile = blockIdx.x;
     if (C::NBUF == 2 || EARLY) issue(tile, 0);
     fill_stage_tw<N, C::P>(tw);
+    op_prologue<N>(op);
     __syncthreads();
     for (int it = 0; tile < tiles; ++it, tile += gridDim.x) {
         int b = 0;
@@ -401,6 +414,7 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, VAR>::THREADS, ColCfgOf<Rl
     int64_t tile = blockIdx.x;
     if (C::NBUF == 2) issue(tile, 0);
     fill_stage_tw<N, C::P>(tw);
+    op_prologue<N>(op);
     __syncthreads();
     for (int it = 0; tile < tiles; ++it, tile += gridDim.x) {
         int b = 0;
@@ -465,6 +479,7 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, 
     const int groups = int(kept_groups(op, nx / C::W)), tiles = groups * int(batch);
     if (threadIdx.x == 0) mbar_init(sbar, 1);
     fill_stage_tw<N, C::P>(tw);
+    op_prologue<N>(op);
     __syncthreads();
     unsigned parity = 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, parity ^= 1u) {
@@ -606,6 +621,7 @@ __global__ void __launch_bounds__(2 * ColCfgOf<Rl, N, Op, 0>::THREADS,
         issue(int(blockIdx.x), 0);
     }
     fill_stage_tw<N, C::P>(tw);
+    op_prologue<N>(op);
     __syncthreads();
 
     const Sm sm[1] = {Sm{xbuf + grp * C::BUF + c * C::STRIDE}};

@@ -103,12 +103,37 @@ def taylor_green_2pi(n: int, t: float = 0.0, nu: float = 1e-3) -> np.ndarray:
     return 2 * np.sin(X) * np.sin(Y) * math.exp(-2 * nu * t)
 
 
+_FIELD_CACHE: dict = {}
+
+
+def _serving_field(eq: str, n: int, seed: int, dtype: str):
+    """A seeded initial state of a serving request, cached: (psi,) for NLS,
+    (u0, v0) for sine-Gordon, (w0,) for Navier-Stokes, in the request's
+    precision (rounded once from FP64)."""
+    key = (eq, n, seed, dtype)
+    got = _FIELD_CACHE.get(key)
+    if got is None:
+        cplx, real = (np.complex64, np.float32) if dtype == "fp32" else (np.complex128, np.float64)
+        if eq == "nls":
+            got = (nls_gaussian(n, seed=seed).astype(cplx),)
+        elif eq == "sg":
+            got = tuple(a.astype(real) for a in sg_gaussian(n, seed=seed))
+        else:
+            got = (ns_power_law(n, seed=seed).astype(real),)
+        _FIELD_CACHE[key] = got
+    return got
+
+
 def serving_mix(count: int, rate_hz: float, sizes=(128, 256, 512, 1024, 2048), steps=(50, 500),
-                seed: int = SEED_BASE + 4, eqs=("nls", "sg", "ns")) -> list[dict]:
-    """Seeded Poisson stream of mixed solves (FP32): arrival times with mean
-    spacing 1/rate_hz, equation, grid size and step count uniform over the
-    given choices, each with its own seeded initial field and the parameters
-    of that equation's workload above."""
+                seed: int = SEED_BASE + 4, eqs=("nls", "sg", "ns"), fields_per_shape: int | None = None,
+                precision: str = "fp32") -> list[dict]:
+    """Seeded Poisson stream of mixed solves: arrival times with mean spacing
+    1/rate_hz, equation, grid size and step count uniform over the given
+    choices, each with the parameters of that equation's workload above.
+    Every request gets its own seeded initial field, or, with
+    fields_per_shape = k, one of k seeded fields of its (equation, N) (a
+    stream of thousands of requests then holds k fields per shape in host
+    memory instead of one per request)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
@@ -118,15 +143,17 @@ def serving_mix(count: int, rate_hz: float, sizes=(128, 256, 512, 1024, 2048), s
         n = int(sizes[int(rng.integers(len(sizes)))])
         k = int(rng.integers(steps[0], steps[1] + 1))
         fseed = int(rng.integers(1 << 30))
+        if fields_per_shape:
+            fseed = seed * 7919 + (fseed % fields_per_shape)
+        state = _serving_field(eq, n, fseed, precision)
         if eq == "nls":
-            state = (nls_gaussian(n, seed=fseed),)
             params = {"dt": 1e-3, "lx": 20 * math.pi, "ly": 20 * math.pi}
         elif eq == "sg":
-            state = sg_gaussian(n, seed=fseed)
             params = {"dt": 1e-3, "lx": 10 * math.pi, "ly": 10 * math.pi, "rfft": 1}
         else:
-            state = (ns_power_law(n, seed=fseed),)
             params = {"dt": 2.5e-4, "lx": 2 * math.pi, "ly": 2 * math.pi, "nu": 1e-3, "rfft": 1}
         out.append({"rid": rid, "eq": eq, "n": n, "steps": k, "state": state, "arrival": t,
-                    "precision": "fp32", "params": params})
+                    "precision": precision, "params": params, "seed": fseed})
+    if not fields_per_shape:
+        _FIELD_CACHE.clear()  # each request holds its own arrays
     return out

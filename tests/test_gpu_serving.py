@@ -98,3 +98,42 @@ def test_step_n_batch_equals_separate_calls(lib, cuda_device):
         assert ga.stats() == gb.stats()
     with pytest.raises(lib.PssError):
         lib.pss_step_n_batch([a[0].h, a[1].h], [1, -1])
+
+
+def _oracle_result(orc, q):
+    """The FP64 oracle's solve of request q from the same (rounded) initial field."""
+    p = dict(q.params)
+    L = p["lx"]
+    if q.eq == "nls":
+        return (orc.nls_run(q.state[0].astype(np.complex128), L, L, p["dt"], q.steps, merged=True),)
+    if q.eq == "sg":
+        un, um = orc.sg_init(q.state[0].astype(np.float64), q.state[1].astype(np.float64), L, L, p["dt"])
+        un, um = orc.sg_run(un, um, L, L, p["dt"], q.steps)
+        return orc.sg_fields(un, um)
+    wh, _, ok = orc.ns_run(orc.ns_init(q.state[0].astype(np.float64), True), L, L, p["nu"], p["dt"], q.steps,
+                           tol=1e-10)
+    assert ok
+    return (orc.ns_field(wh),)
+
+
+def test_mix_up_to_1024_matches_solo_runs_and_oracle(lib, orc, cuda_device):
+    # the serving workload's shapes up to 1024^2 (one pool per equation and
+    # size, 1 to 8 slots each), requests admitted as slots free up; every
+    # result equals its solo run, and for each equation the largest request
+    # also matches the FP64 oracle (FP32 targets: 1e-5, sine-Gordon 2e-5)
+    from paper_1206_3215_gb300.serving import Request, Server
+    reqs = [Request.from_dict(d) for d in S.serving_mix(40, 1e6, sizes=(128, 256, 512, 1024), steps=(10, 40),
+                                                         seed=S.SEED_BASE + 40, fields_per_shape=2)]
+    srv = Server(slots=8, round_max=16)
+    results, stats = srv.run(reqs, realtime=False)
+    srv.close()
+    assert len(results) == len(reqs) and stats["pools"] >= 6
+    _check(results, reqs)
+    for eq in ("nls", "sg", "ns"):
+        mine = [q for q in reqs if q.eq == eq and q.n >= 512]
+        assert mine, eq
+        q = max(mine, key=lambda r: (r.n, -r.steps))
+        got = results[q.rid].state
+        got = got if isinstance(got, tuple) else (got,)
+        for a, b in zip(got, _oracle_result(orc, q)):
+            check(a, b, 2e-5 if eq == "sg" else 1e-5)
