@@ -28,6 +28,12 @@ namespace pss {
 
 template <class V> __device__ __forceinline__ V cadd(V a, V b) { return {a.x + b.x, a.y + b.y}; }
 template <class V> __device__ __forceinline__ V csub(V a, V b) { return {a.x - b.x, a.y - b.y}; }
+// FP32: one packed-pair add per complex add or subtract (each lane rounds as
+// a single add does, so the results are those of two adds; the passes are
+// bound by instruction issue, and the butterflies are mostly adds: measured
+// at 1024^2, row pass 134.8 -> 130.7 us, column pass 155.6 -> 145.5 us)
+template <> __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, float2{-b.x, -b.y}); }
 template <class V> __device__ __forceinline__ V cmul(V a, V b)
 {
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
