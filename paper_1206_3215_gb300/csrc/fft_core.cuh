@@ -116,7 +116,12 @@ template <int RAD, int DIR, int K, class V> __device__ __forceinline__ V rot(V z
         const R dr = sc * z.x - ss * z.y, di = sc * z.y + ss * z.x;
         if constexpr (sizeof(R) == 4) {
             constexpr float hh = float(H), hl = float(H - double(float(H)));
-            return {mul_hl(dr, hh, hl), mul_hl(di, hh, hl)};
+            // both components at once as packed pairs (each lane rounds as
+            // mul_hl does; measured about 1 % off both NLS passes at 1024^2;
+            // the general rotations below stay scalar: their operand pairs
+            // would need swapped copies, and a packed form was 9 % slower)
+            const float2 d{dr, di};
+            return __ffma2_rn(d, float2{hh, hh}, __fmul2_rn(d, float2{hl, hl}));
         } else {
             return {R(H) * dr, R(H) * di};
         }

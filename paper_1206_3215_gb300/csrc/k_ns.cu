@@ -7,19 +7,30 @@ namespace pss {
 // Device-side loop control, 4 ints: [0] update index k of the current pass,
 // [1] any field still active after this update (built by k_ns_decide),
 // [2] the value of [1] at the last k_ns_advance (read by the host loop).
-// one thread per field: fold the partials of update k, decide, count
-__global__ void k_ns_decide(NsField *fs, const double *partials, int64_t groups, int64_t batch, int *ctl,
-                            double parseval, double tol, int max_iter)
+// one block per field: fold the partials of update k in a fixed order (a
+// strided sum per thread, then a tree), decide, count
+constexpr int NS_DECIDE_THREADS = 256;
+__global__ void __launch_bounds__(NS_DECIDE_THREADS)
+    k_ns_decide(NsField *fs, const double *partials, int64_t groups, int64_t batch, int *ctl, double parseval,
+                double tol, int max_iter)
 {
-    const int64_t f = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    __shared__ double red[NS_DECIDE_THREADS];
+    const int64_t f = blockIdx.x;
     if (f >= batch) return;
+    NsField s = fs[f];
+    if (!s.active) return;  // the same for every thread of the block
+    double sum = 0.0;
+    for (int64_t g = threadIdx.x; g < groups; g += NS_DECIDE_THREADS) sum += partials[f * groups + g];
+    red[threadIdx.x] = sum;
+    __syncthreads();
+    for (int w = NS_DECIDE_THREADS / 2; w > 0; w >>= 1) {
+        if (int(threadIdx.x) < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
     const int k = ctl[0];
     int *any_active = ctl + 1;
-    NsField s = fs[f];
-    if (!s.active) return;
-    double sum = 0.0;
-    for (int64_t g = 0; g < groups; ++g) sum += partials[f * groups + g];
-    const double norm = parseval * sum;
+    const double norm = parseval * red[0];
     s.updates += 1;
     const bool done = norm < tol;
     if (done || k + 1 >= max_iter) {
@@ -100,7 +111,7 @@ cudaError_t ns_begin(void *fs, int64_t batch, int *ctl, cudaStream_t s)
 cudaError_t ns_decide(void *fs, const double *partials, int64_t groups, int64_t batch, int *ctl, double parseval,
                       double tol, int max_iter, cudaStream_t s)
 {
-    k_ns_decide<<<unsigned((batch + 255) / 256), 256, 0, s>>>(static_cast<NsField *>(fs), partials, groups,
+    k_ns_decide<<<unsigned(batch), NS_DECIDE_THREADS, 0, s>>>(static_cast<NsField *>(fs), partials, groups,
                                                              batch, ctl, parseval, tol, max_iter);
     return cudaGetLastError();
 }

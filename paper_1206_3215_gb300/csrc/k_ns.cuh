@@ -129,6 +129,22 @@ template <class Rl> struct NsRow {
 // transforms of a real field at -kx are the conjugates of those at kx, with
 // the spectrum taken at -kx), so four inverse transforms per column replace
 // two on twice as many columns.
+// Squared difference d^2 added to the double-float accumulator (hi, lo) in
+// FP32 arithmetic: d^2 = p + e exactly (e by a fused multiply-add), p enters
+// hi by Knuth's two-sum and the rounding errors collect in lo.  The sum keeps
+// about twice the FP32 precision without the FP64 pipe, which on GB300 runs
+// 64 times slower than FP32 and held up the column pass.
+__device__ __forceinline__ void df_add_sq(float &hi, float &lo, float d)
+{
+    const float p = d * d;
+    const float e = __fmaf_rn(d, d, -p);
+    const float sum = hi + p;
+    const float bp = sum - hi;
+    const float err = (hi - (sum - bp)) + (p - bp);
+    hi = sum;
+    lo += err + e;
+}
+
 template <class Rl, bool MID, bool HALF = false> struct NsCol {
     static constexpr int NIN = 1;
     static constexpr bool COL_LAND = true;  // exchanges and the norm partial sync per tile (BLOCK)
@@ -181,6 +197,7 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
         const int xs = valid ? x : 0;  // table index (the padding reads column 0's entries)
         const Rl kx = __ldg(kxo + xs), kxx = __ldg(kx2 + xs), mx = __ldg(keepx + xs);
         double acc = 0.0;
+        float acc_hi = 0.0f, acc_lo = 0.0f;  // FP32: double-float partial of this thread
         if (live) {  // the update reads w^n, w^k (and J_hat^n) after the forward transform
 #pragma unroll
             for (int m = 0; m < P; ++m) {
@@ -237,8 +254,17 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
                     const V2<Rl> inc{(Rl(2) * a * a_n.x + half_dt * (jk.x + jnv.x)) * inv,
                                      (Rl(2) * a * a_n.y + half_dt * (jk.y + jnv.y)) * inv};
                     const V2<Rl> w1v{a_n.x - inc.x, a_n.y - inc.y};
-                    const double ex = double(w1v.x) - double(a_k.x), ey = double(w1v.y) - double(a_k.y);
-                    if (valid) acc += ex * ex + ey * ey;
+                    if constexpr (sizeof(Rl) == 4) {
+                        // w^{k+1} - w^k: exact in FP32 once the iterates agree to a
+                        // factor of two (Sterbenz), one rounding before that
+                        if (valid) {
+                            df_add_sq(acc_hi, acc_lo, w1v.x - a_k.x);
+                            df_add_sq(acc_hi, acc_lo, w1v.y - a_k.y);
+                        }
+                    } else {
+                        const double ex = double(w1v.x) - double(a_k.x), ey = double(w1v.y) - double(a_k.y);
+                        if (valid) acc += ex * ex + ey * ey;
+                    }
                     if (live) wk1[o] = w1v;
                     v[m] = ns_deriv(0, jfield(w1v, a_n), kx, __ldg(kyo + y), kk, inv_n2);
                 }
@@ -273,6 +299,7 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
         }
         // FP64 partial of |w^{k+1} - w^k|^2 over this tile, folded in a fixed order
         const int64_t g = x / W;
+        if constexpr (sizeof(Rl) == 4) acc = double(acc_hi) + double(acc_lo);
         block_partial<BLOCK>(acc, partials + field * (nx / W - skip_n) + (g < skip_lo ? g : g - skip_n));
     }
     // sum over the threads of the tile in a fixed tree; the tile's first
