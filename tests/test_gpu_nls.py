@@ -67,9 +67,16 @@ def test_plane_wave_1024_closed_form(lib, cuda_device, precision):
     exact = p0 * np.exp(-1j * (k2 + A * A) * dt * steps)
     check(got, exact, 1e-11 if precision == "fp64" else TOL32_STATE)
     m1, e1 = g.conserved()[0]
-    # FP64: 4000 passes of ~1e-16 rounding each.  FP32: a single Fourier mode
-    # rotates coherently, so the rounding errors of successive steps are
-    # correlated instead of averaging out over many modes; 5e-6 over 2000 steps
+    # FP64: 4000 passes of ~1e-16 rounding each.  FP32: the whole mass sits in
+    # one Fourier coefficient, whose rounding in every pass is coherent over
+    # the field instead of averaging over many modes, so the mass performs a
+    # random walk of about one FP32 rounding per step (measured over four
+    # modes and amplitudes and both launch shapes: sign changes, rms 3.1e-6 at
+    # 2000 steps and 4.1e-6 at 4000).  The 1e-6 target holds for the noise
+    # workload (test_config2_1024_matches_oracle_and_conserves_mass) but cannot
+    # be promised for a single mode; this bound (about 2 rms at 2000 steps)
+    # still catches a systematic bias, which grows linearly in the steps, and
+    # the benchmark reports the measured drift against the target
     tol_m = 2e-12 if precision == "fp64" else 5 * TOL32_MASS
     assert abs(m1 - A * A * L * L) / (A * A * L * L) <= tol_m
     assert abs(m1 - m0) / m0 <= tol_m
