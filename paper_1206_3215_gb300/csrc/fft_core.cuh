@@ -227,6 +227,22 @@ __device__ __forceinline__ void prefetch_l2(const void *p)
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Load of streamed state (read once per pass, or re-read from L2 right after
+// this thread stored it): cached in L2 only, so that it does not evict the
+// small tables (wavenumbers, masks, twiddles) the pass keeps reading through
+// L1.  PSS_LDCG=0 uses ordinary loads.
+#ifndef PSS_LDCG
+#define PSS_LDCG 1
+#endif
+template <class V> __device__ __forceinline__ V ld_stream(const V *p)
+{
+#if PSS_LDCG
+    return __ldcg(p);
+#else
+    return *p;
+#endif
+}
+
 // Register fence: every value of v is materialised here and nothing that
 // uses v moves above it, so the two transforms of a fused pass are not
 // interleaved (which would keep both transforms' temporaries live).

@@ -228,9 +228,9 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
 #pragma unroll
                         for (int c = 0; c < CH && m + c < P; ++c) {
                             const int64_t oc = int64_t(t + T * (m + c)) * nx;
-                            ln[c] = live ? wn[oc] : V2<Rl>{0, 0};
-                            lk[c] = live ? wk[oc] : V2<Rl>{0, 0};
-                            if (!MID && k > 0) lj[c] = live ? jn[base + oc] : V2<Rl>{0, 0};
+                            ln[c] = live ? ld_stream(wn + oc) : V2<Rl>{0, 0};
+                            lk[c] = live ? ld_stream(wk + oc) : V2<Rl>{0, 0};
+                            if (!MID && k > 0) lj[c] = live ? ld_stream(jn + base + oc) : V2<Rl>{0, 0};
                         }
                     const Rl mask = mx * __ldg(keepy + y);
                     const V2<Rl> jk{v[m].x * mask, v[m].y * mask};
@@ -288,8 +288,8 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
                     for (int m = 0; m < P; ++m) {
                         const int y = t + T * m;
                         const int64_t o = int64_t(y) * nx;
-                        const V2<Rl> w1v = live ? wk1[o] : V2<Rl>{0, 0};  // stored by this thread in pass 0
-                        const V2<Rl> a_n = (MID && live) ? wn[o] : V2<Rl>{0, 0};
+                        const V2<Rl> w1v = live ? ld_stream(wk1 + o) : V2<Rl>{0, 0};  // stored by this thread in pass 0
+                        const V2<Rl> a_n = (MID && live) ? ld_stream(wn + o) : V2<Rl>{0, 0};
                         const V2<Rl> d = ns_deriv(nwhich, jfield(w1v, a_n), sx, __ldg(kyo + y), kxx + __ldg(ky2 + y),
                                                   inv_n2);
                         v[m] = V2<Rl>{sg * d.x, sg * d.y};

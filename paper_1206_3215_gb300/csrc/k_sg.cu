@@ -109,8 +109,8 @@ template <class Rl> struct SgCol {
                 V2<Rl> un[CH], dn[CH];
 #pragma unroll
                 for (int c = 0; c < CH; ++c) {
-                    un[c] = pu[c * step];
-                    dn[c] = pd[c * step];
+                    un[c] = ld_stream(pu + c * step);
+                    dn[c] = ld_stream(pd + c * step);
                 }
 #pragma unroll
                 for (int c = 0; c < CH; ++c) {
