@@ -98,35 +98,38 @@ template <class Rl> struct SgCol {
         }
         auto update = [&]() {
             const Rl kx = __ldg(kx2 + x);
-            // one running pointer per array (T rows apart), so the 2P loads and
-            // stores do not each hold a 64-bit address; loads in chunks of CH
-            // points ahead of that chunk's stores (u and d may alias as far as
-            // the compiler knows, so it would not move a load above a store)
-            constexpr int CH = P < 4 ? P : 4;
-            V2<Rl> *pu = u + base + int64_t(t) * nx, *pd = d + base + int64_t(t) * nx;
+            // û and d of point m + LA are loaded while point m is computed and
+            // stored: the loads are placed before the earlier points' stores
+            // in program order (the compiler keeps loads and stores that may
+            // alias in that order; û, d and h are separate arrays and every
+            // point is its own row, so they do not alias), so LA points are
+            // always in flight instead of waiting one round trip per chunk
+            constexpr int LA = P < 4 ? P : 4;
+            const V2<Rl> *lu = u + base + int64_t(t) * nx, *ld = d + base + int64_t(t) * nx;
+            V2<Rl> *su = u + base + int64_t(t) * nx, *sd = d + base + int64_t(t) * nx;
+            V2<Rl> ru[LA], rd[LA];
 #pragma unroll
-            for (int m0 = 0; m0 < P; m0 += CH) {
-                V2<Rl> un[CH], dn[CH];
+            for (int j = 0; j < LA; ++j, lu += step, ld += step) {
+                ru[j] = ld_stream(lu);
+                rd[j] = ld_stream(ld);
+            }
 #pragma unroll
-                for (int c = 0; c < CH; ++c) {
-                    un[c] = ld_stream(pu + c * step);
-                    dn[c] = ld_stream(pd + c * step);
+            for (int m = 0; m < P; ++m, su += step, sd += step) {
+                const V2<Rl> un = ru[m % LA], dn = rd[m % LA];
+                if (m + LA < P) {
+                    ru[m % LA] = ld_stream(lu);
+                    rd[m % LA] = ld_stream(ld);
+                    lu += step;
+                    ld += step;
                 }
-#pragma unroll
-                for (int c = 0; c < CH; ++c) {
-                    const int m = m0 + c;
-                    const int y = t + T * m;
-                    const Rl a = dt2 * (kx + __ldg(ky2 + y));
-                    const Rl inv = rcp_(Rl(1) + Rl(0.25) * a);
-                    const V2<Rl> dn1{dn[c].x - (a * un[c].x + dt2 * v[m].x) * inv,
-                                     dn[c].y - (a * un[c].y + dt2 * v[m].y) * inv};
-                    const V2<Rl> un1{un[c].x + dn1.x, un[c].y + dn1.y};
-                    pd[c * step] = dn1;
-                    pu[c * step] = un1;
-                    v[m] = cscale(un1, inv_n2);
-                }
-                pu += CH * step;
-                pd += CH * step;
+                const int y = t + T * m;
+                const Rl a = dt2 * (kx + __ldg(ky2 + y));
+                const Rl inv = rcp_(Rl(1) + Rl(0.25) * a);
+                const V2<Rl> dn1{dn.x - (a * un.x + dt2 * v[m].x) * inv, dn.y - (a * un.y + dt2 * v[m].y) * inv};
+                const V2<Rl> un1{un.x + dn1.x, un.y + dn1.y};
+                *sd = dn1;
+                *su = un1;
+                v[m] = cscale(un1, inv_n2);
             }
         };
         if constexpr (sg_shared(sizeof(Rl))) {
