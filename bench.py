@@ -39,6 +39,11 @@ L = 20 * math.pi
 DT = 1e-3
 FP64_NOMINAL_GFLOPS = 1250.0  # nominal GB300 FP64 rate, used only if the measurement fails
 E2E_STEPS = 2000  # one full solve of the 1024^2 configuration per e2e iteration
+# per-pass events around the passes of every S-th timed step, S = max(10,
+# K // 20): about 20 timed passes of each kind in a long run (each event pair
+# in the step graph costs microseconds), at least one in a short one
+def profile_stride(steps: int) -> int:
+    return max(10, steps // 20)
 
 
 def parse():
@@ -336,7 +341,7 @@ def other_paths(stream, rank: int, only=None, autotune: bool = True):
     g.set_state(f)
     tune(g)
     g.step(3)
-    P.pss_set_profiling(g.h, True)
+    P.pss_set_profiling(g.h, profile_stride(K))
     ms = timed_steps(g, K, stream)
     prof = P.pss_profile_read(g.h)
     P.pss_set_profiling(g.h, False)
@@ -445,10 +450,12 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    # timed region: K steps through the library, device-resident state; the
-    # library records an event pair around every pass (per-pass times for the
-    # roofline, on the library's stream)
-    P.pss_set_profiling(g.h, True)
+    # timed region: K steps through the library, device-resident state, run
+    # as the step graphs run them; the library records an event pair around
+    # the row and the column pass of every profile_stride(K)-th step inside the
+    # graph (per-pass times for the roofline, on the library's stream), which
+    # leaves the stepping speed as it is
+    P.pss_set_profiling(g.h, profile_stride(args.steps))
     barrier()
     torch.cuda.synchronize(dev)
     t_timed = time.perf_counter()
@@ -461,8 +468,8 @@ def run_ours(args):
     ms = reduce_max(e0.elapsed_time(e1), dev)
     prof = P.pss_profile_read(g.h)
     P.pss_set_profiling(g.h, False)
-    # the same K steps timed again `repeats` times, as the step graphs run them
-    # (no per-pass events): median, min and max
+    # the same K steps timed again `repeats` times with no events at all:
+    # median, min and max
     reps = []
     for _ in range(args.repeats):
         torch.cuda.synchronize(dev)

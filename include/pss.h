@@ -199,15 +199,20 @@ int pss_checkpoint_size(const pss_grid *g, size_t *bytes);
 int pss_checkpoint_save(pss_grid *g, void *buf, int where);
 int pss_checkpoint_load(pss_grid *g, const void *buf, int where);
 
-/* Pass timing (tracing).  With profiling on, pss_step_n records a CUDA event
- * pair around every row pass and every column pass on the grid's stream.
+/* Pass timing (tracing).  on = 0: off (the default); on = 1: pss_step_n
+ * records a CUDA event pair around every row pass and every column pass on
+ * the grid's stream; on = S > 1: only around the passes of every S-th step
+ * (pass pairs 0, S, 2S, ... of each pss_step_n call), which leaves the
+ * stepping speed as it is (an event pair costs a few microseconds per pass).
+ * NLS and sine-Gordon steps keep running as captured CUDA graphs while
+ * profiling, with the events inside the graph; Navier-Stokes steps run as
+ * direct launches while profiling.
  * pss_profile_read synchronises and writes 7 doubles:
  *   out[0] = kernel launches made by pss_step_n since profiling was switched on,
  *   out[1], out[2] = row passes timed and their total milliseconds,
  *   out[3], out[4] = column passes timed and their total milliseconds,
  *   out[5], out[6] = other step kernels (NS control) timed and total ms.
- * Switching profiling on clears the counters.  Event gaps add a few
- * microseconds per pass; off by default. */
+ * Switching profiling on clears the counters.  Errors: PSS_E_ARG (on < 0). */
 int pss_set_profiling(pss_grid *g, int on);
 int pss_profile_read(pss_grid *g, double *out, int cap, int *count);
 

@@ -211,7 +211,8 @@ def pss_fft2d(ptr: int, nx: int, ny: int, batch: int, precision: int, direction:
         raise PssError(rc, "pss_fft2d failed")
 
 
-def pss_set_profiling(h, on: bool) -> None:
+def pss_set_profiling(h, on: bool | int) -> None:
+    """0/False off; 1/True time every pass; S > 1 time the passes of every S-th step."""
     _check(load_library().pss_set_profiling(h, int(on)), h)
 
 

@@ -285,7 +285,9 @@ int pss_set_profiling(pss_grid *g, int on)
     DeviceGuard dg(g->dev);
     int rc = g->profile_resolve();
     if (rc) return rc;
+    if (on < 0) return g->fail(PSS_E_ARG, "set_profiling: on must be >= 0");
     g->profiling = on != 0;
+    g->prof_stride = on > 1 ? on : 1;
     for (int k = 0; k < 3; ++k) {
         g->prof_ms[k] = 0;
         g->prof_n[k] = 0;

@@ -209,6 +209,20 @@ int pss_grid::pass_begin(int kind)
     ++launches;
     plan_tuning()->open_kind = kind;
     if (!profiling) return PSS_OK;
+    prof_open = sampled(prof_pass++);
+    if (!prof_open) return PSS_OK;
+    if (capturing) {
+        // a profiling graph: an event pair around each timed pass; the graph
+        // owns its events
+        cudaEvent_t e;
+        int rc = cuda(cudaEventCreate(&e), "event create");
+        if (rc) return rc;
+        capturing->evs.push_back(e);
+        capturing->kinds.push_back(kind);
+        // External: a node of the graph that records the event when it runs
+        // (a plain record during capture only orders the captured work)
+        return cuda(cudaEventRecordWithFlags(e, stream, cudaEventRecordExternal), "event record");
+    }
     while (ev_pool.size() < ev_used + 2) {
         cudaEvent_t e;
         int rc = cuda(cudaEventCreate(&e), "event create");
@@ -222,7 +236,15 @@ int pss_grid::pass_begin(int kind)
 int pss_grid::pass_end()
 {
     plan_tuning()->open_kind = -1;
-    if (!profiling) return PSS_OK;
+    if (!profiling || !prof_open) return PSS_OK;
+    prof_open = false;
+    if (capturing) {
+        cudaEvent_t e;
+        int rc = cuda(cudaEventCreate(&e), "event create");
+        if (rc) return rc;
+        capturing->evs.push_back(e);
+        return cuda(cudaEventRecordWithFlags(e, stream, cudaEventRecordExternal), "event record");
+    }
     return cuda(cudaEventRecord(ev_pool[ev_used++], stream), "event record");
 }
 
@@ -230,6 +252,17 @@ int pss_grid::profile_resolve()
 {
     int rc = cuda(cudaStreamSynchronize(stream), "profile sync");
     if (rc) return rc;
+    if (prof_pending) {
+        // timed pass i of the graph ran between its events 2i and 2i + 1
+        const StepGraph &g = *prof_pending;
+        prof_pending = nullptr;
+        for (size_t i = 0; i < g.kinds.size() && 2 * i + 1 < g.evs.size(); ++i) {
+            float ms = 0.f;
+            if ((rc = cuda(cudaEventElapsedTime(&ms, g.evs[2 * i], g.evs[2 * i + 1]), "elapsed"))) return rc;
+            prof_ms[g.kinds[i]] += ms;
+            prof_n[g.kinds[i]] += 1;
+        }
+    }
     for (size_t i = 0; i < ev_kind.size(); ++i) {
         float ms = 0.f;
         if ((rc = cuda(cudaEventElapsedTime(&ms, ev_pool[2 * i], ev_pool[2 * i + 1]), "elapsed"))) return rc;
@@ -974,6 +1007,7 @@ int pss_grid::step_n(int64_t n)
 {
     if (n == 0) return PSS_OK;
     int rc;
+    prof_pass = 0;
     if (graph_epoch != plan_epoch().load()) {  // a plan changed: recapture
         drop_graphs();
         graph_epoch = plan_epoch().load();
@@ -983,26 +1017,37 @@ int pss_grid::step_n(int64_t n)
 #define NLS(R) nls_step<R>(this, n)
 #define SG(R) sg_step<R>(this, n)
 #define NS(R) ns_step<R>(this, n)
-    if (p.eq != PSS_EQ_NS && use_graphs && !profiling) {
-        // the whole launch sequence of step_n(n) as one graph, cached by n
-        cudaGraphExec_t exec = nullptr;
+    if (p.eq != PSS_EQ_NS && use_graphs) {
+        // the whole launch sequence of step_n(n) as one graph, cached by
+        // (n, profiling); a profiling graph's own events time its passes
+        const int prof_key = profiling ? prof_stride : 0;
+        StepGraph *sg = nullptr;
         for (auto &e : step_graphs)
-            if (e.first == n) exec = e.second;
-        if (!exec) {
+            if (e.n == n && e.prof == prof_key) sg = &e;
+        if (sg && sg == prof_pending && (rc = profile_resolve())) return rc;  // its events are reused
+        if (!sg) {
+            StepGraph fresh;
+            fresh.n = n;
+            fresh.prof = prof_key;
             rc = cuda(cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed), "capture");
             if (!rc) {
                 const int64_t saved = launches;
+                if (profiling) capturing = &fresh;
+                prof_pass = 0;
                 int inner = p.eq == PSS_EQ_NLS ? PSS_BY_PRECISION(NLS) : PSS_BY_PRECISION(SG);
+                capturing = nullptr;
+                fresh.passes = launches - saved;
                 launches = saved;
                 cudaGraph_t graph = nullptr;
                 cudaError_t e = cudaStreamEndCapture(stream, &graph);
                 if (inner) rc = inner;
                 else if ((rc = cuda(e, "capture end")) == PSS_OK)
-                    rc = cuda(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+                    rc = cuda(cudaGraphInstantiate(&fresh.exec, graph, 0), "graph instantiate");
                 if (graph) cudaGraphDestroy(graph);
             }
             if (rc) {
                 // capture is not available here: direct launches from now on
+                free_step_graph(fresh);
                 use_graphs = false;
                 cudaGetLastError();
                 err.clear();
@@ -1011,12 +1056,29 @@ int pss_grid::step_n(int64_t n)
                 return rc;
             }
             if (step_graphs.size() >= 4) {
-                cudaGraphExecDestroy(step_graphs.front().second);
+                if (prof_pending) {  // resolve before the list (and the pending entry) moves
+                    if ((rc = profile_resolve())) {
+                        free_step_graph(fresh);
+                        return rc;
+                    }
+                }
+                free_step_graph(step_graphs.front());
                 step_graphs.erase(step_graphs.begin());
             }
-            step_graphs.emplace_back(n, exec);
+            if (prof_pending) {  // the vector may reallocate below
+                if ((rc = profile_resolve())) {
+                    free_step_graph(fresh);
+                    return rc;
+                }
+            }
+            step_graphs.push_back(std::move(fresh));
+            sg = &step_graphs.back();
         }
-        rc = cuda(cudaGraphLaunch(exec, stream), "graph launch");
+        rc = cuda(cudaGraphLaunch(sg->exec, stream), "graph launch");
+        if (!rc) {
+            launches += sg->passes;
+            if (sg->prof) prof_pending = sg;
+        }
     } else {
         rc = p.eq == PSS_EQ_NLS ? PSS_BY_PRECISION(NLS) : p.eq == PSS_EQ_SG ? PSS_BY_PRECISION(SG) : PSS_BY_PRECISION(NS);
     }
@@ -1153,6 +1215,8 @@ int pss_grid::autotune(int k, int *changed)
     }
     int rc = checkpoint(save, PSS_DEVICE, true);
     const bool prof = profiling;
+    const int stride = prof_stride;
+    prof_stride = 1;  // every pass of the tuning steps is timed
     // per variant and pass kind, the best mean pass time over the rounds; round
     // 0 (one step of each variant) only loads the kernels and warms the clocks
     double t[2][2] = {{1e30, 1e30}, {1e30, 1e30}};
@@ -1181,6 +1245,7 @@ int pss_grid::autotune(int k, int *changed)
         }
     *pt = PlanTuning{};
     profiling = prof;
+    prof_stride = stride;
     for (int i = 0; i < 3; ++i) prof_ms[i] = 0, prof_n[i] = 0;
     cudaFree(save);
     if (rc) return rc;

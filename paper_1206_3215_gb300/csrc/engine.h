@@ -60,8 +60,14 @@ struct pss_grid {
     void *ns_field = nullptr;     // device, batch records (see k_ns.cu)
     void *host_fields = nullptr;  // pinned copy of the records
 
-    // tracing: event pairs around passes (kind 0 row, 1 column, 2 other)
+    // tracing: event pairs around passes (kind 0 row, 1 column, 2 other);
+    // with prof_stride S > 1 only the passes of every S-th step are timed
+    // (pass pairs 0, S, 2S, ... of a pss_step_n call)
     bool profiling = false;
+    int prof_stride = 1;
+    int64_t prof_pass = 0;   // passes seen in the current pss_step_n call
+    bool prof_open = false;  // the pass being run is timed
+    bool sampled(int64_t pass) const { return prof_stride <= 1 || (pass / 2) % prof_stride == 0; }
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<int> ev_kind;  // kind of pair i = events 2i, 2i+1
@@ -72,18 +78,41 @@ struct pss_grid {
     int pass_end();
     int profile_resolve();
 
-    // captured CUDA graphs (off while profiling, or with PSS_GRAPHS=0)
+    // captured CUDA graphs (NLS/SG: also while profiling; NS: off while
+    // profiling; all off with PSS_GRAPHS=0)
     bool use_graphs = true;
     cudaGraph_t ns_graph = nullptr;       // one NS step: begin -> WHILE(active) { passes }
     cudaGraphExec_t ns_exec = nullptr;
     cudaGraphConditionalHandle ns_cond = 0;
-    std::vector<std::pair<int64_t, cudaGraphExec_t>> step_graphs;  // NLS/SG step_n(n), by n
+    // NLS/SG step_n(n) as one graph, by (n, profiling stride).  A profiling
+    // graph records an event pair around each timed pass (its own events)
+    // and the kind of each timed pass.
+    struct StepGraph {
+        int64_t n = 0;
+        int prof = 0;  // 0: no events; else the profiling stride
+        cudaGraphExec_t exec = nullptr;
+        int64_t passes = 0;
+        std::vector<cudaEvent_t> evs;
+        std::vector<int> kinds;
+    };
+    std::vector<StepGraph> step_graphs;
+    const StepGraph *prof_pending = nullptr;  // profiling graph launched, not yet read
+    StepGraph *capturing = nullptr;           // profiling graph being captured
     int graph_epoch = 0;  // plan epoch the cached graphs were captured under
+    static void free_step_graph(StepGraph &g)
+    {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        for (cudaEvent_t e : g.evs) cudaEventDestroy(e);
+        g.exec = nullptr;
+        g.evs.clear();
+    }
     void drop_graphs()
     {
         if (ns_exec) cudaGraphExecDestroy(ns_exec);
         if (ns_graph) cudaGraphDestroy(ns_graph);
-        for (auto &g : step_graphs) cudaGraphExecDestroy(g.second);
+        if (prof_pending) cudaStreamSynchronize(stream);  // its events must not be destroyed in flight
+        prof_pending = nullptr;
+        for (auto &g : step_graphs) free_step_graph(g);
         step_graphs.clear();
         ns_exec = nullptr;
         ns_graph = nullptr;

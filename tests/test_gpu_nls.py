@@ -197,3 +197,29 @@ def test_bench_configuration_fields_match_oracle(lib, orc, cuda_device):
         check(got[i], ref, TOL32_STATE)
     m1 = g.conserved()[:, 0]
     assert np.max(np.abs(m1 - m0) / m0) <= TOL32_MASS
+
+
+@pytest.mark.parametrize("graphs", ["1", "0"])
+def test_sampled_pass_profiling(lib, cuda_device, monkeypatch, graphs):
+    # profiling with stride 10 times the passes of every 10th step of a call
+    # (pass pairs 0, 10, 20, ...: a step_n(100) call runs 201 passes, column
+    # half step first), counts every launch, and leaves the results bitwise
+    # those of an unprofiled run, with the step graphs and without
+    monkeypatch.setenv("PSS_GRAPHS", graphs)
+    n, steps = 64, 100
+    p0 = S.nls_gaussian(n)[None]
+    ref = _grid(lib, n, "fp32", dt=1e-3)
+    ref.set_state(p0)
+    ref.step(steps)
+    g = _grid(lib, n, "fp32", dt=1e-3)
+    g.set_state(p0)
+    lib.pss_set_profiling(g.h, 10)
+    g.step(steps)
+    prof = lib.pss_profile_read(g.h)
+    assert prof["launches"] == 2 * steps + 1
+    assert prof["col"][0] == 11 and prof["row"][0] == 10
+    assert prof["col"][1] > 0 and prof["row"][1] > 0
+    lib.pss_set_profiling(g.h, False)
+    assert np.array_equal(g.get_state().view(np.uint32), ref.get_state().view(np.uint32))
+    with pytest.raises(lib.PssError):
+        lib.pss_set_profiling(g.h, -1)
