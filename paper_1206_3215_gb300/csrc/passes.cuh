@@ -455,6 +455,16 @@ template <class Op>
 struct TmaCol<Op, std::void_t<decltype(std::declval<const Op &>().status)>>
     : std::integral_constant<bool, Op::NIN == 1 && !FieldIn<Op>::value> {};
 
+// ops whose col() takes a hook for the start of the last stage of their last
+// transform (COL_EARLY): the one-buffer column pass then issues the next
+// tile's copy there.  PSS_COL_EARLY=0 compiles every op without it.
+#ifndef PSS_COL_EARLY
+#define PSS_COL_EARLY 1
+#endif
+template <class Op, class = void> struct ColEarly : std::false_type {};
+template <class Op>
+struct ColEarly<Op, std::void_t<decltype(Op::COL_EARLY)>> : std::integral_constant<bool, PSS_COL_EARLY && Op::COL_EARLY> {};
+
 // dynamic shared memory of the tensor-copy column pass: the buffer, room to
 // align it to 128 bytes and the mbarrier
 template <class C> constexpr size_t tma_col_smem() { return C::SMEM + 128 + 16; }
@@ -481,17 +491,28 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, 
     fill_stage_tw<N, C::P>(tw);
     op_prologue<N>(op);
     __syncthreads();
+    // thread 0: ask for tile `tl` (the buffer's earlier shared-memory accesses
+    // come first)
+    auto issue = [&](int tl) {
+        if (threadIdx.x != 0 || tl >= tiles) return;
+        const int f = tl / groups;
+        const int xs = int(group_index(op, tl - f * groups)) * C::W;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(sbar, unsigned(N * C::W * sizeof(V)));
+        // skip_copy (host fault injection only): announce the bytes but start
+        // no copy, so that the wait below runs out with nothing in flight
+        if (!skip_copy) tma_load_4d(smem_addr(buf), &map, sbar, 2 * xs, 0, 0, f);
+    };
+    // an op with COL_EARLY calls a hook at the start of the last stage of its
+    // last transform, after its last shared-memory access: the next tile's
+    // copy is issued there and lands under that stage and the tile's stores
+    constexpr bool EARLY = ColEarly<Op>::value;
+    if (EARLY) issue(int(blockIdx.x));
     unsigned parity = 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, parity ^= 1u) {
         const int field = tile / groups;
         const int x0 = int(group_index(op, tile - field * groups)) * C::W;
-        if (threadIdx.x == 0) {
-            fence_proxy_async_smem();  // the previous tile's shared-memory accesses come first
-            mbar_arrive_expect_tx(sbar, unsigned(N * C::W * sizeof(V)));
-            // skip_copy (host fault injection only): announce the bytes but
-            // start no copy, so that the wait below runs out with nothing in flight
-            if (!skip_copy) tma_load_4d(smem_addr(buf), &map, sbar, 2 * x0, 0, 0, field);
-        }
+        if (!EARLY) issue(tile);
         const bool landed = mbar_wait(sbar, parity, wait_limit);
         if (__syncthreads_or(!landed)) {
             if (threadIdx.x == 0) atomicOr(op.status, STATUS_TMA_TIMEOUT);
@@ -501,8 +522,16 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, 
 #pragma unroll
         for (int m = 0; m < C::P; ++m) v[0][m] = buf[(t + C::T * m) * C::W + c];
         const Sm sm[1] = {Sm{buf + c * C::STRIDE}};
-        op.template col<N, C::P, C::BLOCK>(v, int64_t(field), x0 + c, t, sm, tw);
-        fft_sync<C::BLOCK>();  // every read of this tile is done before the next copy lands
+        if constexpr (EARLY) {
+            const int next = tile + int(gridDim.x);
+            op.template col<N, C::P, C::BLOCK>(v, int64_t(field), x0 + c, t, sm, tw, [&]() {
+                fft_sync<C::BLOCK>();  // every shared-memory access of this tile is done
+                issue(next);
+            });
+        } else {
+            op.template col<N, C::P, C::BLOCK>(v, int64_t(field), x0 + c, t, sm, tw);
+            fft_sync<C::BLOCK>();  // every read of this tile is done before the next copy lands
+        }
     }
 }
 

@@ -2,7 +2,9 @@
 with the launch shapes it runs: Navier-Stokes at 4096^2 (Section 4.3, Table
 4's largest grid; Crank-Nicolson and implicit midpoint, full and half
 spectra, 2/3 rule), sine-Gordon at 2048^2 on half spectra (Section 4.2,
-Table 3) and NLS at 4096^2 on broadband noise fields (Section 4.1, Table 2).
+Table 3) and NLS at 4096^2 on broadband noise fields (Section 4.1, Table 2);
+and the benchmark's FP64 lines (sine-Gordon 2048^2, both layouts; NLS 1024^2,
+the 32-field batch).
 
 Each case compares every element of the final state with the FP64 oracle on
 the same seeded fields (relative L2 and the element-wise bound of
@@ -121,4 +123,41 @@ def test_nls_4096_noise_fields_match_oracle(lib, orc, cuda_device, monkeypatch, 
         check(got[i], _nls_reference(i), TOL32)
     m1 = g.conserved()[:, 0]
     assert np.max(np.abs(m1 - m0) / m0) <= 1e-6
+    g.close()
+
+
+# FP64 lines of the benchmark: the same workloads on the plain FP64 path
+TOL64 = 1e-10
+
+
+@pytest.mark.parametrize("rfft", [0, 1])
+def test_sg_2048_fp64_matches_oracle(lib, orc, cuda_device, rfft):
+    # the benchmark's FP64 sine-Gordon batch (4 fields), full and half spectra
+    batch, steps = 4, 5
+    u0, v0 = _sg_inputs()
+    g = lib.Grid("sg", SG_N, "fp64", batch=batch, lx=SG_L, ly=SG_L, x0=-SG_L / 2, y0=-SG_L / 2, dt=SG_DT,
+                 rfft=rfft)
+    g.set_state(u0[:batch], v0[:batch])
+    g.step(steps)
+    a, b = g.get_state()
+    for f in (0, batch - 1):
+        un, um = orc.sg_init(u0[f], v0[f], SG_L, SG_L, SG_DT)
+        un, um = orc.sg_run(un, um, SG_L, SG_L, SG_DT, steps)
+        ref_n, ref_m = orc.sg_fields(un, um)
+        check(a[f], ref_n, TOL64)
+        check(b[f], ref_m, TOL64)
+    g.close()
+
+
+def test_nls_1024_fp64_bench_batch_matches_oracle(lib, orc, cuda_device):
+    # the benchmark's FP64 line: 32 fields of 1024^2 in one batch; the first
+    # and the last field after 20 steps against the oracle
+    n, B, L, dt, steps = 1024, 32, 20 * math.pi, 1e-3, 20
+    f = S.nls_gaussian(n, seed=S.SEED_BASE + 1, batch=B)
+    g = lib.Grid("nls", n, "fp64", batch=B, lx=L, ly=L, x0=-L / 2, y0=-L / 2, dt=dt)
+    g.set_state(f)
+    g.step(steps)
+    got = g.get_state()
+    for i in (0, B - 1):
+        check(got[i], orc.nls_run(f[i], L, L, dt, steps, merged=True), TOL64)
     g.close()
