@@ -161,8 +161,10 @@ int pss_grid::init()
     const size_t parts = size_t(batch) * 3 * std::max<int64_t>(RED_BLOCKS, nx);
     if ((rc = alloc((void **)&partials, parts * 8))) return rc;
     if ((rc = alloc((void **)&sums, size_t(batch) * 3 * 8))) return rc;
-    if ((rc = alloc((void **)&flags, 64))) return rc;
-    if ((rc = cuda(cudaMemset(flags, 0, 64), "memset"))) return rc;
+    // NS: the per-tile words of the split column pass follow the 64-byte block
+    const size_t flag_bytes = 64 + (p.eq == PSS_EQ_NS ? size_t(batch) * size_t(nx) * 4 : 0);
+    if ((rc = alloc((void **)&flags, flag_bytes))) return rc;
+    if ((rc = cuda(cudaMemset(flags, 0, flag_bytes), "memset"))) return rc;
     void *hp = nullptr;
     if ((rc = cuda(cudaMallocHost(&hp, size_t(batch) * 3 * 8 + 64), "cudaMallocHost"))) return rc;
     owned_host.push_back(hp);

@@ -135,5 +135,12 @@ constexpr unsigned FLAG_NOT_CONVERGED = 2u;
 // int slot of the grid's 64-byte device flag block that pass kernels report
 // a lost tile copy in (slots 0 .. 3 carry the NS step control)
 constexpr int FLAG_SLOT_PASS_STATUS = 8;
+// NS split column pass: slot 4 its item counter (zeroed by k_ns_begin and
+// k_ns_advance), slot 5 the column-pass epoch (never reset; k_ns_advance
+// adds one), and from int FLAG_TILE_DONE on one word per column tile
+// (batch x nx words, allocated after the 64-byte block for NS grids)
+constexpr int FLAG_SLOT_SPLIT_CLAIM = 4;
+constexpr int FLAG_SLOT_EPOCH = 5;
+constexpr int FLAG_TILE_DONE = 16;
 
 }  // namespace pss

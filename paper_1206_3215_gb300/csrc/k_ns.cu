@@ -6,7 +6,9 @@ namespace pss {
 
 // Device-side loop control, 4 ints: [0] update index k of the current pass,
 // [1] any field still active after this update (built by k_ns_decide),
-// [2] the value of [1] at the last k_ns_advance (read by the host loop).
+// [2] the value of [1] at the last k_ns_advance (read by the host loop); and
+// the split column pass's item counter and epoch (FLAG_SLOT_SPLIT_CLAIM,
+// FLAG_SLOT_EPOCH).
 // one block per field: fold the partials of update k in a fixed order (a
 // strided sum per thread, then a tree), decide, count
 constexpr int NS_DECIDE_THREADS = 256;
@@ -49,6 +51,7 @@ __global__ void k_ns_begin(NsField *fs, int64_t batch, int *ctl)
     if (f == 0) {
         ctl[0] = 0;
         ctl[1] = 0;
+        ctl[FLAG_SLOT_SPLIT_CLAIM] = 0;
     }
     if (f < batch) fs[f].active = 1;
 }
@@ -62,6 +65,8 @@ __global__ void k_ns_advance(int *ctl, int use_graph, cudaGraphConditionalHandle
     ctl[2] = more;
     ctl[1] = 0;
     ctl[0] += 1;
+    ctl[FLAG_SLOT_SPLIT_CLAIM] = 0;  // the next column pass claims its items from 0
+    ctl[FLAG_SLOT_EPOCH] += 1;       // and publishes its tiles under a new value
     if (use_graph) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 

@@ -70,6 +70,15 @@ __host__ __device__ __forceinline__ int ns_buf(int idx, int k)
     return k == 0 ? idx : (idx + 1 + ((k - 1) & 1)) % 3;
 }
 
+// Products and fused multiply-adds with their roundings written out: the
+// column pass's arithmetic is inlined into several kernels (one-part and
+// split passes, per-point staging), and a compiler free to contract a * b + c
+// may fuse a different product in each; with these they agree bit for bit.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // packed derivative spectra of w_hat at wavenumber (kx, ky) (odd-derivative
 // wavenumbers: zero at the Nyquist index), times the inverse-transform scale:
 // which = 0: C1 = (kx + i ky) psi_hat, psi_hat = w_hat / |k|^2 (0 at k = 0);
@@ -78,10 +87,10 @@ template <class V, class R> __device__ __forceinline__ V ns_deriv(int which, V w
 {
     if (which == 0) {
         const R inv = k2 > R(0) ? s / k2 : R(0);
-        const V p{w.x * inv, w.y * inv};  // psi_hat * s
-        return V{kx * p.x - ky * p.y, kx * p.y + ky * p.x};
+        const V p{mul_rn(w.x, inv), mul_rn(w.y, inv)};  // psi_hat * s
+        return V{fma_rn(kx, p.x, -mul_rn(ky, p.y)), fma_rn(kx, p.y, mul_rn(ky, p.x))};
     }
-    return V{-(kx * w.y + ky * w.x) * s, (kx * w.x - ky * w.y) * s};
+    return V{mul_rn(-fma_rn(kx, w.y, mul_rn(ky, w.x)), s), mul_rn(fma_rn(kx, w.x, -mul_rn(ky, w.y)), s)};
 }
 
 // The row pass keeps both inputs in registers (measured at 4096^2: 0.22 ms
@@ -136,7 +145,7 @@ template <class Rl> struct NsRow {
 // 64 times slower than FP32 and held up the column pass.
 __device__ __forceinline__ void df_add_sq(float &hi, float &lo, float d)
 {
-    const float p = d * d;
+    const float p = __fmul_rn(d, d);  // rounded on its own: the sum below must not fuse it
     const float e = __fmaf_rn(d, d, -p);
     const float sum = hi + p;
     const float bp = sum - hi;
@@ -148,6 +157,12 @@ __device__ __forceinline__ void df_add_sq(float &hi, float &lo, float d)
 template <class Rl, bool MID, bool HALF = false> struct NsCol {
     static constexpr int NIN = 1;
     static constexpr bool COL_LAND = true;  // exchanges and the norm partial sync per tile (BLOCK)
+    // half spectra, one-buffer shapes (4096 points and more): each tile runs
+    // in two parts (k_col_split), the update with C1's two outputs and C2's
+    // two outputs.  Measured at 4096^2 (column pass per update, CN): batch 1
+    // 351 -> 299 us, batch 2 587 -> 504 us; with full spectra, where the
+    // second part is one transform, 307 -> 318 us, so those stay in one part
+    static constexpr bool COL_SPLIT = HALF;
     static constexpr bool LEAN = NS_LEAN;
     static constexpr int PMAX = NS_PMAX;
     static constexpr int NOUT = HALF ? 4 : 2;  // inverse transforms per column
@@ -168,6 +183,11 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
     // derivative fields; the pass does not visit them (0, 0 without dealiasing)
     int64_t skip_lo, skip_n;
     int *status;  // set when a tile copy did not arrive
+    // split column pass (k_col_split): item counter (zero at launch), epoch of
+    // this pass (the published value is *epoch + 1), per-tile done words
+    int *claim;
+    const int *epoch;
+    unsigned *tile_done;
     static constexpr bool midpoint = MID;  // implicit midpoint, else trapezoidal Jacobian
     __host__ __device__ const V2<Rl> *in(int) const { return c1; }
     __device__ V2<Rl> *wb(int b) const { return b == 0 ? w0 : b == 1 ? w1 : w2; }
@@ -175,15 +195,31 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
     // midpoint (w^{k+1} + w^n)/2
     __device__ __forceinline__ V2<Rl> jfield(V2<Rl> w1v, V2<Rl> a_n) const
     {
-        if constexpr (MID) return V2<Rl>{Rl(0.5) * (w1v.x + a_n.x), Rl(0.5) * (w1v.y + a_n.y)};
+        if constexpr (MID) return V2<Rl>{mul_rn(Rl(0.5), w1v.x + a_n.x), mul_rn(Rl(0.5), w1v.y + a_n.y)};
         return w1v;
     }
     template <int N, int P, int BLOCK, class Sm>
     __device__ __forceinline__ void col(V2<Rl> (&vv)[1][P], int64_t field, int x, int t,
                                         const Sm (&sm)[1], const TW<Rl> *tw) const
     {
+        col_range<N, P, BLOCK>(vv[0], field, x, t, sm[0], tw, 0, NOUT);
+    }
+    // the two parts of a tile in the split column pass (k_col_split): part 0
+    // the update and the outputs of C1, part 1 those of C2, rebuilt from the
+    // iterate part 0 stored
+    template <int N, int P, int BLOCK, class Sm>
+    __device__ __forceinline__ void col_part(V2<Rl> (&vv)[1][P], int64_t field, int x, int t,
+                                             const Sm (&sm)[1], const TW<Rl> *tw, int part) const
+    {
+        col_range<N, P, BLOCK>(vv[0], field, x, t, sm[0], tw, part ? NOUT / 2 : 0, part ? NOUT : NOUT / 2);
+    }
+    // outputs o0 .. o1 - 1 of the column (o0 = 0: v holds the staged column of
+    // J; the update comes first and the partial of the norm is written)
+    template <int N, int P, int BLOCK, class Sm>
+    __device__ __forceinline__ void col_range(V2<Rl> (&v)[P], int64_t field, int x, int t, const Sm &sm,
+                                              const TW<Rl> *tw, int o0, int o1) const
+    {
         constexpr int T = N / P;
-        V2<Rl>(&v)[P] = vv[0];
         const int k = *kptr;
         const NsField f = fs[field];
         const int64_t nxf = in_stride;
@@ -198,7 +234,7 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
         const Rl kx = __ldg(kxo + xs), kxx = __ldg(kx2 + xs), mx = __ldg(keepx + xs);
         double acc = 0.0;
         float acc_hi = 0.0f, acc_lo = 0.0f;  // FP32: double-float partial of this thread
-        if (live) {  // the update reads w^n, w^k (and J_hat^n) after the forward transform
+        if (live && o0 == 0) {  // the update reads w^n, w^k (and J_hat^n) after the forward transform
 #pragma unroll
             for (int m = 0; m < P; ++m) {
                 const int64_t o = int64_t(t + T * m) * nx;
@@ -207,14 +243,35 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
                 if (!MID && k > 0) prefetch_l2(jn + base + o);
             }
         }
-        // pass 0: J_hat and the update; passes 1 .. NOUT: the derivative fields
-        // of the new iterate (or of the midpoint), inverse transforms through
-        // the forward body; each later one is rebuilt from the iterate this
-        // thread has just stored
+        // pass 0: J_hat and the update; pass p > 0: output p - 1, a derivative
+        // field of the new iterate (or of the midpoint), inverse transformed
+        // through the forward body.  Pass 0 leaves the field of output 0 in
+        // v; every later one is rebuilt from the iterate stored in pass 0
+        // (loads that bypass L1: part 1 of the split pass may run on another
+        // SM than the part that stored it)
 #pragma unroll 1
-        for (int pass = 0; pass <= NOUT; ++pass) {
+        for (int pass = o0 == 0 ? 0 : o0 + 1; pass <= o1; ++pass) {
+            if (pass >= 2) {
+                const int out = pass - 1;
+                const int nwhich = HALF ? out >> 1 : out;
+                const bool nmirror = HALF && (out & 1);
+                const Rl sx = nmirror ? -kx : kx;
+                // at -kx a field's transform is conj(IFFT(conj(d(-kx, -ky)) w_hat(kx, ky))):
+                // d(-kx, ky) itself for C1, its negative for C2 = i (kx + i ky) w_hat
+                const Rl sg = (nmirror && nwhich == 1) ? Rl(-1) : Rl(1);
+#pragma unroll
+                for (int m = 0; m < P; ++m) {
+                    const int y = t + T * m;
+                    const int64_t o = int64_t(y) * nx;
+                    const V2<Rl> w1v = live ? __ldcg(wk1 + o) : V2<Rl>{0, 0};
+                    const V2<Rl> a_n = (MID && live) ? ld_stream(wn + o) : V2<Rl>{0, 0};
+                    const V2<Rl> d = ns_deriv(nwhich, jfield(w1v, a_n), sx, __ldg(kyo + y), kxx + __ldg(ky2 + y),
+                                              inv_n2);
+                    v[m] = V2<Rl>{sg * d.x, sg * d.y};
+                }
+            }
             if (pass > 0) conj_all(v);
-            block_fft<N, P, -1, BLOCK>(v, sm[0], t, tw);
+            block_fft<N, P, -1, BLOCK>(v, sm, t, tw);
             if (pass == 0) {
                 // loads of CH points ahead of their stores (the buffers may alias
                 // as far as the compiler knows, so it would not reorder them)
@@ -232,8 +289,8 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
                             lk[c] = live ? ld_stream(wk + oc) : V2<Rl>{0, 0};
                             if (!MID && k > 0) lj[c] = live ? ld_stream(jn + base + oc) : V2<Rl>{0, 0};
                         }
-                    const Rl mask = mx * __ldg(keepy + y);
-                    const V2<Rl> jk{v[m].x * mask, v[m].y * mask};
+                    const Rl mask = mul_rn(mx, __ldg(keepy + y));
+                    const V2<Rl> jk{mul_rn(v[m].x, mask), mul_rn(v[m].y, mask)};
                     // midpoint: jk is already J((w^k + w^n)/2), used twice below
                     V2<Rl> jnv = jk;
                     if constexpr (!MID) {
@@ -249,10 +306,11 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
                     // w^{k+1} = [(1 - a) w^n - dt/2 (J^k + J^n)] / (1 + a), a = dt nu |k|^2 / 2,
                     // formed as w^n minus a small increment so that FP32 rounds
                     // the increment, not the nearly-unit decay factor, every step
-                    const Rl a = half_dt_nu * kk;
+                    const Rl a = mul_rn(half_dt_nu, kk);
                     const Rl inv = ns_rcp(Rl(1) + a);  // correctly rounded, as 1 / (1 + a)
-                    const V2<Rl> inc{(Rl(2) * a * a_n.x + half_dt * (jk.x + jnv.x)) * inv,
-                                     (Rl(2) * a * a_n.y + half_dt * (jk.y + jnv.y)) * inv};
+                    const Rl a2 = Rl(2) * a;           // exact
+                    const V2<Rl> inc{mul_rn(fma_rn(a2, a_n.x, mul_rn(half_dt, jk.x + jnv.x)), inv),
+                                     mul_rn(fma_rn(a2, a_n.y, mul_rn(half_dt, jk.y + jnv.y)), inv)};
                     const V2<Rl> w1v{a_n.x - inc.x, a_n.y - inc.y};
                     if constexpr (sizeof(Rl) == 4) {
                         // w^{k+1} - w^k: exact in FP32 once the iterates agree to a
@@ -277,30 +335,14 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
                 const bool dup = mirror && (x == 0 || 2 * int64_t(x) == nxf);
                 V2<Rl> *dst = (which == 0 ? c1 : c2) + field * N * nxf + (mirror ? nxf - x : x);
                 store_line<P, T>(v, dst, nxf, t, live && !dup);
-                if (pass < NOUT) {
-                    const int nwhich = HALF ? pass >> 1 : pass;
-                    const bool nmirror = HALF && (pass & 1);
-                    const Rl sx = nmirror ? -kx : kx;
-                    // at -kx a field's transform is conj(IFFT(conj(d(-kx, -ky)) w_hat(kx, ky))):
-                    // d(-kx, ky) itself for C1, its negative for C2 = i (kx + i ky) w_hat
-                    const Rl sg = (nmirror && nwhich == 1) ? Rl(-1) : Rl(1);
-#pragma unroll
-                    for (int m = 0; m < P; ++m) {
-                        const int y = t + T * m;
-                        const int64_t o = int64_t(y) * nx;
-                        const V2<Rl> w1v = live ? ld_stream(wk1 + o) : V2<Rl>{0, 0};  // stored by this thread in pass 0
-                        const V2<Rl> a_n = (MID && live) ? ld_stream(wn + o) : V2<Rl>{0, 0};
-                        const V2<Rl> d = ns_deriv(nwhich, jfield(w1v, a_n), sx, __ldg(kyo + y), kxx + __ldg(ky2 + y),
-                                                  inv_n2);
-                        v[m] = V2<Rl>{sg * d.x, sg * d.y};
-                    }
-                }
             }
         }
-        // FP64 partial of |w^{k+1} - w^k|^2 over this tile, folded in a fixed order
-        const int64_t g = x / W;
-        if constexpr (sizeof(Rl) == 4) acc = double(acc_hi) + double(acc_lo);
-        block_partial<BLOCK>(acc, partials + field * (nx / W - skip_n) + (g < skip_lo ? g : g - skip_n));
+        if (o0 == 0) {
+            // FP64 partial of |w^{k+1} - w^k|^2 over this tile, folded in a fixed order
+            const int64_t g = x / W;
+            if constexpr (sizeof(Rl) == 4) acc = double(acc_hi) + double(acc_lo);
+            block_partial<BLOCK>(acc, partials + field * (nx / W - skip_n) + (g < skip_lo ? g : g - skip_n));
+        }
     }
     // sum over the threads of the tile in a fixed tree; the tile's first
     // thread writes.  BLOCK <= 1: the tile is the CTA; BLOCK > 1: a group of
@@ -428,7 +470,8 @@ cudaError_t ns_col_run(V2<Rl> *c1, V2<Rl> *c2, V2<Rl> *const w[3], V2<Rl> *jn, v
     using Op = NsCol<Rl, MID, HALF>;
     Op op{c1, c2, w[0], w[1], w[2], jn, static_cast<NsField *>(fs), partials, kxo, kyo, kx2, ky2,
           keepx, keepy, Rl(0.5 * dt), Rl(0.5 * dt * nu), Rl(1.0 / (double(nxf) * double(ny))), sx, ctl, 0,
-          nxf, 0, 0, const_cast<int *>(ctl) + FLAG_SLOT_PASS_STATUS};
+          nxf, 0, 0, const_cast<int *>(ctl) + FLAG_SLOT_PASS_STATUS, const_cast<int *>(ctl) + FLAG_SLOT_SPLIT_CLAIM,
+          ctl + FLAG_SLOT_EPOCH, reinterpret_cast<unsigned *>(const_cast<int *>(ctl) + FLAG_TILE_DONE)};
     switch (ny) {
 #define PSS_CASE(N)                                                                          \
     case N:                                                                                  \

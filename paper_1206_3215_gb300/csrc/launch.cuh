@@ -14,13 +14,15 @@ namespace pss {
 // Supported lengths of either grid axis.
 #define PSS_FOR_EACH_N(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(8192)
 
-// Opt a kernel into more than 48 KB of dynamic shared memory, once per
-// device (attributes belong to the device's context).  done_mask is a static
-// of the caller, one per kernel instance.
+// Allow a kernel `bytes` of dynamic shared memory, once per device
+// (attributes belong to the device's context).  done_mask is a static of the
+// caller, one per kernel instance.
 template <class K>
 inline cudaError_t allow_smem(K kernel, size_t bytes, std::atomic<unsigned> &done_mask)
 {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    // the 48 KB a kernel has without opting in count its static shared
+    // memory too, so any dynamic request opts in (once per device)
+    if (bytes == 0) return cudaSuccess;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -199,6 +201,49 @@ inline cudaError_t launch_col_land(Op op, const TW<Rl> *tw, int64_t nx, int64_t 
     return cudaGetLastError();
 }
 
+// PSS_COL_SPLIT=0 keeps the one-part column pass for ops that opted into the
+// split one (read per launch)
+inline bool split_enabled()
+{
+    const char *e = getenv("PSS_COL_SPLIT");
+    return !(e && e[0] == '0' && e[1] == 0);
+}
+
+// the split column pass: an op that opted in, in the one-buffer shapes
+// (where the landing-buffer pass does not fit)
+template <class Rl, int N, class Op> constexpr bool split_col()
+{
+    return tma_col<Rl, N, Op>() && SplitOp<Op>::value && ColCfgOf<Rl, N, Op, 0>::BLOCK == 1 &&
+           !land_col<Rl, N, Op>();
+}
+
+template <class Rl, int N, class Op>
+inline cudaError_t launch_col_split(Op op, const TW<Rl> *tw, int64_t nx, int64_t batch, cudaStream_t s)
+{
+    using C = ColCfgOf<Rl, N, Op, 0>;
+    auto k = k_col_split<Rl, N, Op>;
+    constexpr size_t smem = tma_col_smem<C>();
+    static std::atomic<unsigned> done{0};
+    static int ctas[32] = {};
+    cudaError_t e = allow_smem(k, smem, done);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = kept_groups(op, nx / C::W) * batch;
+    if (tiles <= 0) return cudaSuccess;
+    // the kernel counts items (two per tile) and claims them in 32 bits
+    if (tiles > (INT32_MAX - 2 * 65536) / 2) return cudaErrorInvalidValue;
+    CUtensorMap map;
+    if ((e = encode_col_map(&map, op.in(0), int(sizeof(V2<Rl>)), in_stride(op, nx), N, batch, C::W)) != cudaSuccess)
+        return e;
+    int grid = 0;
+    if ((e = resident_ctas(k, C::THREADS, smem, ctas, &grid)) != cudaSuccess) return e;
+    if (2 * tiles < grid) grid = int(2 * tiles);
+    const char *f = getenv("PSS_FAULT");
+    const bool inject = f && strcmp(f, "tma_timeout") == 0;
+    k<<<dim3(unsigned(grid)), C::THREADS, smem, s>>>(map, op, tw, nx, batch, inject ? 64u : TMA_WAIT_LIMIT,
+                                                      inject ? 1 : 0);
+    return cudaGetLastError();
+}
+
 template <class Rl, int N, class Op>
 inline cudaError_t launch_row_n(Op op, const TW<Rl> *tw, int64_t rows_total, cudaStream_t s)
 {
@@ -220,6 +265,8 @@ inline cudaError_t launch_col_n(Op op, const TW<Rl> *tw, int64_t nx, int64_t bat
     }
     if constexpr (land_col<Rl, N, Op>())
         if (tma_enabled() && land_enabled()) return launch_col_land<Rl, N, Op>(op, tw, nx, batch, s);
+    if constexpr (split_col<Rl, N, Op>())
+        if (tma_enabled() && split_enabled()) return launch_col_split<Rl, N, Op>(op, tw, nx, batch, s);
     if constexpr (tma_col<Rl, N, Op>())
         if (tma_enabled()) return launch_col_tma<Rl, N, Op>(op, tw, nx, batch, s);
     return launch_col_v<Rl, N, Op, 0>(op, tw, nx, batch, s);

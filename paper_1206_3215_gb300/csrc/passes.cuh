@@ -536,6 +536,139 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, 
 }
 
 // ----------------------------------------------------------------------------
+// Column pass in two parts per tile, for ops whose tile work is long and whose
+// tiles are few (Navier-Stokes at batch 1: 342 tiles of four 4096-point
+// columns on 152 SMs, one tile per SM at a time, are 2.25 rounds, so the
+// last third of the pass ran on a quarter of the SMs).  Work item i < tiles
+// is part 0 of tile i (its tensor copy, then op.col_part(..., 0)); item
+// tiles + i is part 1 (op.col_part(..., 1)), which reads what part 0 stored.
+// CTAs claim positions in increasing order from a counter (op.claim, zero at
+// launch); split_item maps them to items so that part 1 of a tile comes
+// about one item's time after its part 0 (its stores are then done, and
+// still in L2), and always after it.  So whenever a CTA holds part 1 of a
+// tile, part 0 has been claimed by a running CTA, and part 0 never waits on
+// another item: every wait ends.
+// Part 0 publishes its stores (CTA barrier, fence, release store of the
+// pass's epoch into the tile's word op.tile_done[i]); part 1 polls that word
+// with acquire loads, bounded: if it never comes it sets STATUS_SPLIT_TIMEOUT
+// and returns.  An op opts in with COL_SPLIT = true.
+template <class Op, class = void> struct SplitOp : std::false_type {};
+template <class Op>
+struct SplitOp<Op, std::void_t<decltype(Op::COL_SPLIT)>> : std::integral_constant<bool, Op::COL_SPLIT> {};
+
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+// polls of a part-1 wait, 256 ns apart: about a second
+constexpr unsigned SPLIT_WAIT_LIMIT = 1u << 22;
+
+// Claim position p (0 <= p < 2 tiles) -> (part, tile), with a lag of `lag`
+// tiles (1 <= lag <= tiles): part 0 of tiles 0 .. lag - 1, then part 0 of
+// tile lag + j and part 1 of tile j alternately, then the last parts 1.
+// Part 1 of tile j sits at lag + 2 j + 1, after part 0 of tile j (at j or
+// at 2 j - lag < j + lag + 1).
+__host__ __device__ __forceinline__ void split_item(int p, int tiles, int lag, int &part, int &tile)
+{
+    const int mixed = 2 * (tiles - lag);
+    if (p < lag) {
+        part = 0;
+        tile = p;
+    } else if (p < lag + mixed) {
+        const int q = p - lag;
+        part = q & 1;
+        tile = part ? q >> 1 : lag + (q >> 1);
+    } else {
+        part = 1;
+        tile = tiles - lag + (p - lag - mixed);
+    }
+}
+constexpr int STATUS_SPLIT_TIMEOUT = 2;
+
+template <class Rl, int N, class Op>
+__global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, N, Op, 0>::MIN_CTAS)
+    k_col_split(const __grid_constant__ CUtensorMap map, Op op, const TW<Rl> *__restrict__ tw, int64_t nx,
+                int64_t batch, unsigned wait_limit, int skip_copy)
+{
+    using C = ColCfgOf<Rl, N, Op, 0>;
+    using V = V2<Rl>;
+    using Sm = SmemLine<V, C::PADLOG>;
+    static_assert(C::NBUF == 1 && C::BLOCK == 1, "one staging buffer; transforms span the CTA");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *const buf = reinterpret_cast<V *>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
+    const unsigned sbar = smem_addr(buf + C::BUF);
+    __shared__ int item_s;
+    const int c = threadIdx.x % C::W, t = threadIdx.x / C::W;
+    const int groups = int(kept_groups(op, nx / C::W)), tiles = groups * int(batch);
+    const unsigned epoch = unsigned(*op.epoch) + 1u;
+    if (threadIdx.x == 0) mbar_init(sbar, 1);
+    fill_stage_tw<N, C::P>(tw);
+    op_prologue<N>(op);
+    __syncthreads();
+    unsigned parity = 0;
+    const int lag = imin(int(gridDim.x), tiles);
+    for (;;) {
+        if (threadIdx.x == 0) item_s = atomicAdd(op.claim, 1);
+        __syncthreads();
+        const int pos = item_s;  // rewritten only after the barrier at the end of this item
+        if (pos >= 2 * tiles) break;
+        int part, tile;
+        split_item(pos, tiles, lag, part, tile);
+        const int field = tile / groups;
+        const int x0 = int(group_index(op, tile - field * groups)) * C::W;
+        const Sm sm[1] = {Sm{buf + c * C::STRIDE}};
+        V v[1][C::P];
+        if (part == 0) {
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(sbar, unsigned(N * C::W * sizeof(V)));
+                // skip_copy (host fault injection only): no copy is started
+                if (!skip_copy) tma_load_4d(smem_addr(buf), &map, sbar, 2 * x0, 0, 0, field);
+            }
+            const bool landed = mbar_wait(sbar, parity, wait_limit);
+            parity ^= 1u;
+            if (__syncthreads_or(!landed)) {
+                if (threadIdx.x == 0) atomicOr(op.status, STATUS_TMA_TIMEOUT);
+                return;
+            }
+#pragma unroll
+            for (int m = 0; m < C::P; ++m) v[0][m] = buf[(t + C::T * m) * C::W + c];
+            op.template col_part<N, C::P, C::BLOCK>(v, int64_t(field), x0 + c, t, sm, tw, 0);
+            __syncthreads();  // every store of part 0 has been made
+            if (threadIdx.x == 0) {
+                __threadfence();
+                st_release_gpu(op.tile_done + tile, epoch);
+            }
+        } else {
+            bool ok = true;
+            if (threadIdx.x == 0) {
+                ok = false;
+                for (unsigned i = 0; i < SPLIT_WAIT_LIMIT; ++i) {
+                    if (ld_acquire_gpu(op.tile_done + tile) == epoch) {
+                        ok = true;
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+                __threadfence();
+            }
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicOr(op.status, STATUS_SPLIT_TIMEOUT);
+                return;
+            }
+            op.template col_part<N, C::P, C::BLOCK>(v, int64_t(field), x0 + c, t, sm, tw, 1);
+        }
+        fft_sync<C::BLOCK>();  // the buffer's readers are done before the next copy lands
+    }
+}
+
+// ----------------------------------------------------------------------------
 // Tensor-copy column pass whose copies overlap the transforms.  With one
 // staging buffer (k_col_tma) a CTA asks for its next tile only when it has
 // finished the current one, so every copy's latency is exposed to that CTA.

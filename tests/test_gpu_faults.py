@@ -71,3 +71,32 @@ def test_lost_tile_copy_is_reported_and_handle_recovers(lib, cuda_device, monkey
     assert np.array_equal(got.view(np.uint32), ref.get_state().view(np.uint32))
     g.close()
     ref.close()
+
+
+def test_lost_tile_copy_in_the_split_column_pass(lib, cuda_device, monkeypatch):
+    # Navier-Stokes at 4096^2 runs its column pass in two parts per tile: the
+    # first parts' copies never arrive, so every CTA gives up on its first
+    # item (no second part is claimed, nothing waits on it); the state is
+    # reported lost, and the handle steps again, bit for bit as a fresh grid
+    n, Ln = 4096, 2 * math.pi
+    w0 = S.ns_power_law(n)
+    kw = dict(lx=Ln, ly=Ln, dt=2.5e-4, nu=1e-3, dealias=1, rfft=1)
+    monkeypatch.setenv("PSS_FAULT", "tma_timeout")
+    g = lib.Grid("ns", n, "fp32", **kw)
+    g.set_state(w0[None])
+    with pytest.raises(lib.PssError) as e:
+        g.step(2)
+        g.sync()
+    assert e.value.code == lib.PSS_E_CUDA
+    assert "tile copy" in str(e.value)
+    monkeypatch.delenv("PSS_FAULT")
+    g.set_state(w0[None])
+    g.step(2)
+    g.sync()
+    ref = lib.Grid("ns", n, "fp32", **kw)
+    ref.set_state(w0[None])
+    ref.step(2)
+    assert np.array_equal(g.get_state().view(np.uint32), ref.get_state().view(np.uint32))
+    assert g.stats()[1] == ref.stats()[1]  # set_state restarts the update count
+    g.close()
+    ref.close()

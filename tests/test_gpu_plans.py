@@ -145,3 +145,31 @@ def test_tensor_copy_staging_is_bitwise_equal_ns(lib, cuda_device, monkeypatch, 
     for other in out[1:]:
         assert out[0][1] == other[1]
         assert np.array_equal(np.ascontiguousarray(out[0][0]).view(np.uint8), np.ascontiguousarray(other[0]).view(np.uint8))
+
+
+@pytest.mark.parametrize("batch", [1, 2])
+@pytest.mark.parametrize("scheme", ["cn", "midpoint"])
+def test_split_column_pass_is_bitwise_equal_ns(lib, cuda_device, monkeypatch, batch, scheme):
+    # 4096^2, half spectra: the column pass runs each tile in two parts claimed
+    # from a counter (the second part, C2, waits for the first's stores); the
+    # one-part tensor-copy pass (PSS_COL_SPLIT=0) and per-point staging
+    # (PSS_TMA=0) agree with it bit for bit, also in the fixed-point
+    # decisions.  Batch 2: the parts of one field's tiles and the next
+    # field's interleave
+    rfft = 1
+    n, Ln, nu, dt = 4096, 2 * math.pi, 1e-3, 2.5e-4
+    w0 = S.ns_power_law(n, batch=batch)
+    out = []
+    for tma, split in (("1", "1"), ("1", "0"), ("0", "0")):
+        monkeypatch.setenv("PSS_TMA", tma)
+        monkeypatch.setenv("PSS_COL_SPLIT", split)
+        g = lib.Grid("ns", n, "fp32", batch=batch, lx=Ln, ly=Ln, dt=dt, nu=nu, dealias=1, rfft=rfft,
+                     scheme=scheme)
+        g.set_state(w0)
+        g.step(3)
+        g.sync()
+        out.append((g.get_state(), g.stats()[1]))
+        g.close()
+    for other in out[1:]:
+        assert out[0][1] == other[1]
+        assert np.array_equal(np.ascontiguousarray(out[0][0]).view(np.uint8), np.ascontiguousarray(other[0]).view(np.uint8))
