@@ -218,13 +218,15 @@ template <class Rl> struct NlsCol {
     // at 4096^2, 790 -> 761 us at 8192^2; the SG and NS column ops were slower
     // with it)
     static constexpr bool COL_EARLY = true;
+    // in place: the landing-buffer pass stores each tile with one tensor copy
+    static constexpr bool COL_TMA_STORE = true;
     V2<Rl> *data;
     int64_t nx;
     Rl scale;
     const TW<Rl> *ax, *by;  // exp(-i kx^2 tau) - 1, exp(-i ky^2 tau) - 1
     int *status;            // set when a tile copy did not arrive
     __host__ __device__ const V2<Rl> *in(int) const { return data; }
-    template <int N, int P, int BLOCK, class Sm, class H = NoHook>
+    template <int N, int P, int BLOCK, class Sm, class H = NoHook, bool STORE = true>
     __device__ __forceinline__ void col(V2<Rl> (&vv)[1][P], int64_t field, int x, int t,
                                         const Sm (&smm)[1], const TW<Rl> *tw, const H &hook = H{}) const
     {
@@ -298,7 +300,7 @@ template <class Rl> struct NlsCol {
             fence(v);
             block_fft<N, P, +1, BLOCK>(v, sm, t, tw, hook);
         }
-        store_line<P, T>(v, p, nx, t, true);
+        if constexpr (STORE) store_line<P, T>(v, p, nx, t, true);
     }
 };
 

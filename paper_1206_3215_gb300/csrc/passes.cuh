@@ -688,13 +688,27 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, 
 template <class Op, class = void> struct LandOp : std::false_type {};
 template <class Op>
 struct LandOp<Op, std::void_t<decltype(Op::COL_LAND)>> : std::integral_constant<bool, Op::COL_LAND> {};
+// An op with COL_TMA_STORE = true whose output tile is its input tile (in
+// place) lets the landing-buffer pass store it: col<..., STORE = false>
+// leaves the results in registers, the group writes them into its exchange
+// buffer as the dense [N][W] block of the input copy, and one thread stores
+// that block with one tensor copy (the same map and coordinates) in place of
+// every thread's strided stores of 8-byte points.
+template <class Op, class = void> struct TmaStoreOp : std::false_type {};
+template <class Op>
+struct TmaStoreOp<Op, std::void_t<decltype(Op::COL_TMA_STORE)>> : std::integral_constant<bool, Op::COL_TMA_STORE> {};
+
+// elements between the two groups' exchange buffers: a multiple of 128 bytes,
+// so that each can be the aligned source of a tensor store
+template <class C> constexpr int land_gbuf() { return (C::BUF * int(C::SMEM / C::BUF) + 127) / 128 * 128 / int(C::SMEM / C::BUF); }
 
 // dynamic shared memory: two exchange buffers and the landing buffer, room to
 // align them to 128 bytes, two mbarriers and the control words (abort flag,
 // copies issued towards each group)
 template <class C> constexpr size_t land_col_smem()
 {
-    return 2 * C::SMEM + size_t(C::T) * C::P * C::W * (C::SMEM / C::BUF) + 128 + 16 + 16;
+    return 2 * size_t(land_gbuf<C>()) * (C::SMEM / C::BUF) + size_t(C::T) * C::P * C::W * (C::SMEM / C::BUF) + 128 +
+           16 + 16;
 }
 
 // OR of `v` over the G threads of this thread's group (named barrier id)
@@ -753,9 +767,11 @@ __global__ void __launch_bounds__(2 * ColCfgOf<Rl, N, Op, 0>::THREADS,
     using Sm = SmemLine<V, C::PADLOG>;
     constexpr int G = C::THREADS;  // threads per group
     static_assert(C::NBUF == 1 && G % 32 == 0 && 2 * G <= 1024, "two groups of one-buffer tiles");
+    constexpr bool TST = TmaStoreOp<Op>::value;
+    constexpr int GB = land_gbuf<C>();  // elements per group buffer (128-byte multiple)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *const xbuf = reinterpret_cast<V *>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
-    V *const land = xbuf + 2 * C::BUF;                  // the dense [N][W] landing block
+    V *const land = xbuf + 2 * GB;                      // the dense [N][W] landing block
     const unsigned sbar = smem_addr(land + N * C::W);   // mbarrier of group g at sbar + 8 g
     const unsigned ctrl = sbar + 16;                    // [0] abort, [1 + g] copies issued towards group g
     const int grp = threadIdx.x / G, tg = threadIdx.x % G;
@@ -786,7 +802,7 @@ __global__ void __launch_bounds__(2 * ColCfgOf<Rl, N, Op, 0>::THREADS,
     op_prologue<N>(op);
     __syncthreads();
 
-    const Sm sm[1] = {Sm{xbuf + grp * C::BUF + c * C::STRIDE}};
+    const Sm sm[1] = {Sm{xbuf + grp * GB + c * C::STRIDE}};
     unsigned par = 0;
     for (int tile = int(blockIdx.x) + grp * int(gridDim.x); tile < tiles; tile += 2 * int(gridDim.x), par ^= 1u) {
         const bool landed = mbar_wait_or_abort(sbar + 8 * grp, par, wait_limit, ctrl);
@@ -801,8 +817,12 @@ __global__ void __launch_bounds__(2 * ColCfgOf<Rl, N, Op, 0>::THREADS,
                     if (n > 0) mbar_wait(sbar + 8 * g, unsigned(n - 1) & 1u, wait_limit);
                 }
             }
+            if (TST && tg == 0) bulk_wait();  // this group's stores are done with its buffer
             return;
         }
+        // the group's previous tensor store has read its buffer before the
+        // group's next exchange writes (a group barrier comes in between)
+        if (TST && tg == 0) bulk_wait_read();
         V v[1][C::P];
 #pragma unroll
         for (int m = 0; m < C::P; ++m) v[0][m] = land[(t + C::T * m) * C::W + c];
@@ -810,8 +830,23 @@ __global__ void __launch_bounds__(2 * ColCfgOf<Rl, N, Op, 0>::THREADS,
         if (tg == 0) issue(tile + int(gridDim.x), grp ^ 1);
         const int field = tile / groups;
         const int x0 = int(group_index(op, tile - field * groups)) * C::W;
-        op.template col<N, C::P, G>(v, int64_t(field), x0 + c, t, sm, tw);
+        if constexpr (TST) {
+            op.template col<N, C::P, G, Sm, NoHook, false>(v, int64_t(field), x0 + c, t, sm, tw, NoHook{});
+            V *const dense = xbuf + grp * GB;
+            fft_sync<G>();  // the group's last exchange reads are done
+#pragma unroll
+            for (int m = 0; m < C::P; ++m) dense[(t + C::T * m) * C::W + c] = v[0][m];
+            fence_proxy_async_smem();
+            fft_sync<G>();
+            if (tg == 0) {
+                tma_store_4d(&map, smem_addr(dense), 2 * x0, 0, 0, field);
+                bulk_commit();
+            }
+        } else {
+            op.template col<N, C::P, G>(v, int64_t(field), x0 + c, t, sm, tw);
+        }
     }
+    if (TST && tg == 0) bulk_wait();
 }
 
 // ----------------------------------------------------------------------------

@@ -80,6 +80,23 @@ __device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap *map
         : "memory");
 }
 
+// 4D tiled copy shared -> global of one box (the same tensor map and
+// coordinates as the load of that box), tracked in this thread's bulk-async
+// group; the source must be 128-byte aligned and its writes made visible to
+// the copy engine first (fence_proxy_async_smem by the writers, then a barrier)
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, unsigned src, int c0, int c1, int c2, int c3)
+{
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(src), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// until this thread's committed stores have read their shared-memory source
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// until they have completed
+__device__ __forceinline__ void bulk_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // iterations of mbar_wait before a tile copy counts as lost (each try_wait
 // call may itself suspend for a while: this is seconds, not cycles)
 constexpr unsigned TMA_WAIT_LIMIT = 1u << 24;
