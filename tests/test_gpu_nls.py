@@ -75,11 +75,16 @@ def test_plane_wave_1024_closed_form(lib, cuda_device, precision):
     # 2000 steps and 4.1e-6 at 4000).  The 1e-6 target holds for the noise
     # workload (test_config2_1024_matches_oracle_and_conserves_mass) but cannot
     # be promised for a single mode; this bound (about 2 rms at 2000 steps)
-    # still catches a systematic bias, which grows linearly in the steps, and
-    # the benchmark reports the measured drift against the target
+    # still catches a systematic bias, which grows linearly in the steps; the
+    # 1e-6 target itself is asserted below and, where this run's walk ends
+    # above it, reported as an expected failure with the figure (the
+    # benchmark's accuracy record carries the same figure and target_met)
     tol_m = 2e-12 if precision == "fp64" else 5 * TOL32_MASS
-    assert abs(m1 - A * A * L * L) / (A * A * L * L) <= tol_m
-    assert abs(m1 - m0) / m0 <= tol_m
+    drift = max(abs(m1 - A * A * L * L) / (A * A * L * L), abs(m1 - m0) / m0)
+    assert drift <= tol_m
+    if precision == "fp32" and drift > TOL32_MASS:
+        pytest.xfail(f"FP32 single-mode mass drift {drift:.2e} after {steps} steps is above the 1e-6 target: "
+                     "target not met (rounding random walk of one coefficient)")
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

@@ -2,9 +2,9 @@
 with the launch shapes it runs: Navier-Stokes at 4096^2 (Section 4.3, Table
 4's largest grid; Crank-Nicolson and implicit midpoint, full and half
 spectra, 2/3 rule), sine-Gordon at 2048^2 on half spectra (Section 4.2,
-Table 3) and NLS at 4096^2 on broadband noise fields (Section 4.1, Table 2);
-and the benchmark's FP64 lines (sine-Gordon 2048^2, both layouts; NLS 1024^2,
-the 32-field batch).
+Table 3) and NLS at 4096^2 and 8192^2 on broadband noise fields (Section
+4.1, Table 2); and the benchmark's FP64 lines (sine-Gordon 2048^2, both
+layouts; NLS 1024^2, the 32-field batch).
 
 Each case compares every element of the final state with the FP64 oracle on
 the same seeded fields (relative L2 and the element-wise bound of
@@ -123,6 +123,19 @@ def test_nls_4096_noise_fields_match_oracle(lib, orc, cuda_device, monkeypatch, 
         check(got[i], _nls_reference(i), TOL32)
     m1 = g.conserved()[:, 0]
     assert np.max(np.abs(m1 - m0) / m0) <= 1e-6
+    g.close()
+
+
+def test_nls_8192_noise_field_matches_oracle(lib, orc, cuda_device):
+    # the largest grid (Table 2's 8192^2) on a broadband field: its transforms
+    # end in a radix-8 stage, and its column pass takes two-column tiles
+    n, steps = 8192, 5
+    f = S.nls_gaussian(n, seed=S.SEED_BASE + 5)
+    ref = orc.nls_run(f, NLS_L, NLS_L, NLS_DT, steps, merged=True)
+    g = lib.Grid("nls", n, "fp32", lx=NLS_L, ly=NLS_L, x0=-NLS_L / 2, y0=-NLS_L / 2, dt=NLS_DT)
+    g.set_state(f[None].astype(np.complex64))
+    g.step(steps)
+    check(g.get_state()[0], ref, TOL32)
     g.close()
 
 
