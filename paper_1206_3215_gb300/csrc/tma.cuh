@@ -80,6 +80,21 @@ __device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap *map
         : "memory");
 }
 
+// Ask for the 4D box at these coordinates to be brought into L2 (no shared
+// memory, no completion to wait for): a later copy of the box then reads L2
+__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap *map, int c0, int c1, int c2, int c3)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+                 : "memory");
+}
+// the same for `bytes` (a multiple of 16) contiguous bytes from p (16-byte aligned)
+__device__ __forceinline__ void bulk_prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // 4D tiled copy shared -> global of one box (the same tensor map and
 // coordinates as the load of that box), tracked in this thread's bulk-async
 // group; the source must be 128-byte aligned and its writes made visible to
