@@ -599,8 +599,10 @@ def run_ours(args):
             traj.append([target, float((gp.conserved()[0, 0] - pm0) / pm0)])
         gp.close()
         d2000 = abs(dict((k, v) for k, v in traj)[2000])
-        plane = {"mass_drift_rel_at_steps": traj, "steps": 2000, "mass_drift_rel": d2000, "target": 1e-6,
-                 "target_met": d2000 <= 1e-6,
+        dmax = max(abs(v) for _, v in traj)
+        # the target is judged on the worst of the recorded step counts
+        plane = {"mass_drift_rel_at_steps": traj, "steps": 2000, "mass_drift_rel": d2000,
+                 "mass_drift_rel_max": dmax, "target": 1e-6, "target_met": dmax <= 1e-6,
                  "note": "single Fourier mode: FP32 rounding of its coefficient is not averaged over the field; "
                          "the drift is a random walk (sign changes, ~sqrt(steps)), not a bias"}
 
