@@ -346,6 +346,33 @@ template <int N, int P> __device__ __forceinline__ void fill_stage_tw(const floa
 }
 template <int N, int P> __device__ __forceinline__ void fill_stage_tw(const double2 *) {}
 
+// Last-stage twiddles of FP32 transforms with several butterflies per thread
+// (Q > 1: three or more stages) as W_N^{t r} (loaded) times W_P^{q r} (a
+// compile-time rotation): R - 1 table loads per thread instead of Q (R - 1),
+// and a 16-byte-per-thread footprint of the table instead of the whole last
+// stage's.  Each factor is applied with one rounding of its exact hi + lo
+// value.  PSS_TW_FACTOR=0 loads every product from the table.
+#ifndef PSS_TW_FACTOR
+#define PSS_TW_FACTOR 1
+#endif
+template <int P, int DIR, int Q, int RR, int q, class V, class W>
+__device__ __forceinline__ void fact_rot(V *v, const W &w)
+{
+    if constexpr (q < Q) {
+        v[q + RR * Q] = rot<P, DIR, (q * RR) % P>(twmul<DIR>(v[q + RR * Q], w));
+        fact_rot<P, DIR, Q, RR, q + 1>(v, w);
+    }
+}
+template <int P, int DIR, int Q, int R, int RR, class V, class W>
+__device__ __forceinline__ void fact_stage(V *v, const W *__restrict__ tw, int t)
+{
+    if constexpr (RR < R) {
+        const W w = __ldg(tw + t * RR);
+        fact_rot<P, DIR, Q, RR, 0>(v, w);
+        fact_stage<P, DIR, Q, R, RR + 1>(v, tw, t);
+    }
+}
+
 // One Stockham stage s of a length-N transform (DIR = -1 forward, +1 inverse).
 // On entry register m holds element t + T m of the stage input; on exit (for
 // the last stage) register m holds output element t + T m.  Other stages leave
@@ -360,9 +387,11 @@ __device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const 
     if constexpr (S > 0) {
         // twiddles W_{NS R}^{(j mod NS) r} = W_N^{(j mod NS) r N/(NS R)}
         constexpr bool SMEM = S == 1 && std::is_same<W, float4>::value && StageTw<N, P>::ON;
+        constexpr bool FACT = PSS_TW_FACTOR && LAST && !SMEM && Q > 1 && std::is_same<W, float4>::value;
+        static_assert(!FACT || NS == T * Q, "last stage: jm = t + T q");
         tw = launder(tw);
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
+        for (int q = 0; q < (FACT ? 0 : Q); ++q) {
             const int jm = (t + q * T) & (NS - 1);
             if constexpr (SMEM) {
                 static_assert(NS == StageTw<N, P>::NS && R == StageTw<N, P>::R, "stage 1 shape");
@@ -379,7 +408,7 @@ __device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const 
                     if (r + TWD < R) ring[(r - 1) % TWD] = lds_f4(a0 + unsigned((r + TWD - 1) * NS) * 16u);
                     v[q + r * Q] = twmul<DIR>(v[q + r * Q], w);
                 }
-            } else {
+            } else if constexpr (!FACT) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
                     const W w = __ldg(tw + jm * r * (N / (NS * R)));
@@ -387,6 +416,10 @@ __device__ __forceinline__ void fft_stage(V (&v)[P], const Sm &sm, int t, const 
                 }
             }
         }
+        // the last stage (span NS = N / R = T Q): jm = t + T q, so
+        // W_N^{jm r} = W_N^{t r} W_P^{q r}: R - 1 loads per thread and a
+        // constant rotation per butterfly
+        if constexpr (FACT) fact_stage<P, DIR, Q, R, 1>(v, tw, t);
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q) dft_dif<R, DIR, Q>(v + q);
