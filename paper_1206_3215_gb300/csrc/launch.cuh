@@ -132,8 +132,9 @@ template <class Rl, int N, class Op>
 inline cudaError_t launch_col_tma(Op op, const TW<Rl> *tw, int64_t nx, int64_t batch, cudaStream_t s)
 {
     using C = ColCfgOf<Rl, N, Op, 0>;
+    using HS = TmaHalfStore<Rl, N, Op>;
     auto k = k_col_tma<Rl, N, Op>;
-    constexpr size_t smem = tma_col_smem<C>();
+    constexpr size_t smem = HS::SMEM;
     static std::atomic<unsigned> done{0};
     static int ctas[32] = {};
     cudaError_t e = allow_smem(k, smem, done);
@@ -141,9 +142,17 @@ inline cudaError_t launch_col_tma(Op op, const TW<Rl> *tw, int64_t nx, int64_t b
     const int64_t tiles = kept_groups(op, nx / C::W) * batch;
     if (tiles <= 0) return cudaSuccess;
     if (tiles > INT32_MAX - 2 * 65536) return cudaErrorInvalidValue;  // the kernel counts tiles in 32 bits
-    CUtensorMap map;
+    CUtensorMap map, map_half;
     if ((e = encode_col_map(&map, op.in(0), int(sizeof(V2<Rl>)), in_stride(op, nx), N, batch, C::W)) != cudaSuccess)
         return e;
+    // the half-tile store box (the op writes its input array in place)
+    if constexpr (HS::ON) {
+        if ((e = encode_col_map(&map_half, op.in(0), int(sizeof(V2<Rl>)), in_stride(op, nx), N, batch, C::W, 2)) !=
+            cudaSuccess)
+            return e;
+    } else {
+        map_half = map;
+    }
     int grid = 0;
     if ((e = resident_ctas(k, C::THREADS, smem, ctas, &grid)) != cudaSuccess) return e;
     if (tiles < grid) grid = int(tiles);
@@ -152,7 +161,7 @@ inline cudaError_t launch_col_tma(Op op, const TW<Rl> *tw, int64_t nx, int64_t b
     // returns (a bounded wait that runs out; nothing is left in flight)
     const char *f = getenv("PSS_FAULT");
     const bool inject = f && strcmp(f, "tma_timeout") == 0;
-    k<<<dim3(unsigned(grid)), C::THREADS, smem, s>>>(map, op, tw, nx, batch, inject ? 64u : TMA_WAIT_LIMIT,
+    k<<<dim3(unsigned(grid)), C::THREADS, smem, s>>>(map, map_half, op, tw, nx, batch, inject ? 64u : TMA_WAIT_LIMIT,
                                                       inject ? 1 : 0);
     return cudaGetLastError();
 }

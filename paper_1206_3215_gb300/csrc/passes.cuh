@@ -98,6 +98,11 @@ namespace pss {
 #ifndef PSS_ROW_PREFETCH
 #define PSS_ROW_PREFETCH 1
 #endif
+// one-buffer column passes with an early copy store their tiles by tensor
+// copy through a half-tile staging area (PSS_COL_HALF_STORE=0: strided stores)
+#ifndef PSS_COL_HALF_STORE
+#define PSS_COL_HALF_STORE 1
+#endif
 #ifndef PSS_MAX_NBUF64
 #define PSS_MAX_NBUF64 2
 #endif
@@ -484,13 +489,40 @@ struct ColEarly<Op, std::void_t<decltype(Op::COL_EARLY)>> : std::integral_consta
 // align it to 128 bytes and the mbarrier
 template <class C> constexpr size_t tma_col_smem() { return C::SMEM + 128 + 16; }
 
+// An op with COL_TMA_STORE = true whose output tile is its input tile (in
+// place) lets the pass store its tiles by tensor copy: col<..., STORE = false>
+// leaves the results in registers, the threads write them into shared memory
+// as the dense [N][W] block of the input copy (or halves of it), and one
+// thread stores that with one tensor copy in place of every thread's strided
+// stores of 8-byte points.  The landing-buffer pass stages a tile in the
+// group's exchange buffer; the one-buffer pass with an early copy, whose
+// buffer then already receives the next tile, in a staging area of half a
+// tile, stored in two halves (4096^2: 135 KB buffer + 64 KB staging).
+template <class Op, class = void> struct TmaStoreOp : std::false_type {};
+template <class Op>
+struct TmaStoreOp<Op, std::void_t<decltype(Op::COL_TMA_STORE)>> : std::integral_constant<bool, Op::COL_TMA_STORE> {};
+
+// the one-buffer pass's staging: on for an early-copy op that stores by tensor
+// copy, where a column tile splits into two halves of whole row blocks
+template <class Rl, int N, class Op> struct TmaHalfStore {
+    using C = ColCfgOf<Rl, N, Op, 0>;
+    static constexpr int R = N < 256 ? N : 256;
+    // (one CTA per SM: the staging would not fit beside a second CTA)
+    static constexpr bool ON = PSS_COL_HALF_STORE && TmaStoreOp<Op>::value && ColEarly<Op>::value &&
+                               sizeof(Rl) == 4 && C::MIN_CTAS == 1 && N >= 512 && (N / R) % 2 == 0;
+    static constexpr int HALF_BLOCKS = (N / R) / 2;  // row blocks of R rows per half
+    static constexpr size_t BYTES = ON ? size_t(N / 2) * C::W * sizeof(V2<Rl>) : 0;
+    static constexpr size_t SMEM = tma_col_smem<C>() + (ON ? 128 + BYTES : 0);
+};
+
 
 template <class Rl, int N, class Op>
 __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, N, Op, 0>::MIN_CTAS)
-    k_col_tma(const __grid_constant__ CUtensorMap map, Op op, const TW<Rl> *__restrict__ tw, int64_t nx,
-              int64_t batch, unsigned wait_limit, int skip_copy)
+    k_col_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap map_half, Op op,
+              const TW<Rl> *__restrict__ tw, int64_t nx, int64_t batch, unsigned wait_limit, int skip_copy)
 {
     using C = ColCfgOf<Rl, N, Op, 0>;
+    using HS = TmaHalfStore<Rl, N, Op>;
     using V = V2<Rl>;
     using Sm = SmemLine<V, C::PADLOG>;
     static_assert(C::NBUF == 1, "one staging buffer");
@@ -498,8 +530,11 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, 
     // align to 128 bytes by an offset from the shared array itself (an
     // address rebuilt from an integer would lose the shared state space and
     // turn every exchange access into a generic one)
-    V *const buf = reinterpret_cast<V *>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
+    const unsigned pad = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
+    V *const buf = reinterpret_cast<V *>(smem_raw + pad);
     const unsigned sbar = smem_addr(buf + C::BUF);
+    // the half-tile staging area (HS::ON), 128-byte aligned after the mbarrier
+    V *const stg = reinterpret_cast<V *>(smem_raw + pad + (size_t(C::BUF) * sizeof(V) + 16 + 127) / 128 * 128);
     const int c = threadIdx.x % C::W, t = threadIdx.x / C::W;
     // 32-bit tile counters (the launcher checks the count): fewer live registers
     const int groups = int(kept_groups(op, nx / C::W)), tiles = groups * int(batch);
@@ -531,7 +566,10 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, 
         if (!EARLY) issue(tile);
         const bool landed = mbar_wait(sbar, parity, wait_limit);
         if (__syncthreads_or(!landed)) {
-            if (threadIdx.x == 0) atomicOr(op.status, STATUS_TMA_TIMEOUT);
+            if (threadIdx.x == 0) {
+                atomicOr(op.status, STATUS_TMA_TIMEOUT);
+                if (HS::ON) bulk_wait();  // this CTA's stores are done with the staging area
+            }
             return;
         }
         V v[1][C::P];
@@ -548,15 +586,36 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, 
         const Sm sm[1] = {Sm{buf + c * C::STRIDE}};
         if constexpr (EARLY) {
             const int next = tile + int(gridDim.x);
-            op.template col<N, C::P, C::BLOCK>(v, int64_t(field), x0 + c, t, sm, tw, [&]() {
+            const auto hook = [&]() {
                 fft_sync<C::BLOCK>();  // every shared-memory access of this tile is done
                 issue(next);
-            });
+            };
+            if constexpr (HS::ON) {
+                op.template col<N, C::P, C::BLOCK, Sm, decltype(hook), false>(v, int64_t(field), x0 + c, t, sm, tw,
+                                                                               hook);
+                // rows h N/2 + t + T m (m < P/2) of half h: its register m + h P/2
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (threadIdx.x == 0) bulk_wait_read();  // the staging area's last store has read it
+                    __syncthreads();
+#pragma unroll
+                    for (int m = 0; m < C::P / 2; ++m) stg[(t + C::T * m) * C::W + c] = v[0][h * (C::P / 2) + m];
+                    fence_proxy_async_smem();
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        tma_store_4d(&map_half, smem_addr(stg), 2 * x0, 0, h * HS::HALF_BLOCKS, field);
+                        bulk_commit();
+                    }
+                }
+            } else {
+                op.template col<N, C::P, C::BLOCK>(v, int64_t(field), x0 + c, t, sm, tw, hook);
+            }
         } else {
             op.template col<N, C::P, C::BLOCK>(v, int64_t(field), x0 + c, t, sm, tw);
             fft_sync<C::BLOCK>();  // every read of this tile is done before the next copy lands
         }
     }
+    if (HS::ON && threadIdx.x == 0) bulk_wait();
 }
 
 // ----------------------------------------------------------------------------
@@ -712,15 +771,6 @@ __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, 
 template <class Op, class = void> struct LandOp : std::false_type {};
 template <class Op>
 struct LandOp<Op, std::void_t<decltype(Op::COL_LAND)>> : std::integral_constant<bool, Op::COL_LAND> {};
-// An op with COL_TMA_STORE = true whose output tile is its input tile (in
-// place) lets the landing-buffer pass store it: col<..., STORE = false>
-// leaves the results in registers, the group writes them into its exchange
-// buffer as the dense [N][W] block of the input copy, and one thread stores
-// that block with one tensor copy (the same map and coordinates) in place of
-// every thread's strided stores of 8-byte points.
-template <class Op, class = void> struct TmaStoreOp : std::false_type {};
-template <class Op>
-struct TmaStoreOp<Op, std::void_t<decltype(Op::COL_TMA_STORE)>> : std::integral_constant<bool, Op::COL_TMA_STORE> {};
 
 // elements between the two groups' exchange buffers: a multiple of 128 bytes,
 // so that each can be the aligned source of a tensor store

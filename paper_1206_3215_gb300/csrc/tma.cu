@@ -6,7 +6,8 @@
 
 namespace pss {
 
-cudaError_t encode_col_map(CUtensorMap *map, const void *base, int esz, int64_t nx, int64_t ny, int64_t batch, int w)
+cudaError_t encode_col_map(CUtensorMap *map, const void *base, int esz, int64_t nx, int64_t ny, int64_t batch, int w,
+                           int parts)
 {
     using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -22,10 +23,11 @@ cudaError_t encode_col_map(CUtensorMap *map, const void *base, int esz, int64_t 
     if (esz != 8 && esz != 16) return cudaErrorInvalidValue;
     const int64_t r = ny < 256 ? ny : 256;
     const int64_t real = esz / 2;  // bytes of one real
-    if (ny % r || (w * esz) % 16 || nx % w || w * 2 > 256 || ny / r > 256) return cudaErrorInvalidValue;
+    if (ny % r || (w * esz) % 16 || nx % w || w * 2 > 256 || ny / r > 256 || parts < 1 || (ny / r) % parts)
+        return cudaErrorInvalidValue;
     const cuuint64_t dims[4] = {cuuint64_t(2 * nx), cuuint64_t(r), cuuint64_t(ny / r), cuuint64_t(batch)};
     const cuuint64_t strides[3] = {cuuint64_t(nx * esz), cuuint64_t(r * nx * esz), cuuint64_t(ny * nx * esz)};
-    const cuuint32_t box[4] = {cuuint32_t(2 * w), cuuint32_t(r), cuuint32_t(ny / r), 1};
+    const cuuint32_t box[4] = {cuuint32_t(2 * w), cuuint32_t(r), cuuint32_t(ny / r / parts), 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUresult cr = encode(map, real == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
                                const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

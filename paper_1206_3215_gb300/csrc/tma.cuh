@@ -121,8 +121,10 @@ constexpr unsigned TMA_WAIT_LIMIT = 1u << 24;
 constexpr int STATUS_TMA_TIMEOUT = 1;
 
 // Host: the column-tile tensor map of a [batch][ny][nx] complex array of
-// element size esz (8: complex64, 16: complex128), for tiles of w columns.
+// element size esz (8: complex64, 16: complex128), for tiles of w columns;
+// with parts > 1 the box is 1/parts of a column tile tall (its row blocks
+// start at block (ny / R / parts) h for part h).
 cudaError_t encode_col_map(CUtensorMap *map, const void *base, int esz, int64_t nx, int64_t ny, int64_t batch,
-                           int w);
+                           int w, int parts = 1);
 
 }  // namespace pss
