@@ -173,3 +173,38 @@ def test_split_column_pass_is_bitwise_equal_ns(lib, cuda_device, monkeypatch, ba
     for other in out[1:]:
         assert out[0][1] == other[1]
         assert np.array_equal(np.ascontiguousarray(out[0][0]).view(np.uint8), np.ascontiguousarray(other[0]).view(np.uint8))
+
+
+def test_split_column_pass_with_fields_converging_apart(lib, cuda_device, monkeypatch):
+    # 4096^2 half spectra, two fields, the second 1e-4 times the first: its
+    # fixed point converges in fewer updates, so later updates run the split
+    # column pass with one field inactive (its parts skip their loads and
+    # stores).  Split and one-part passes agree bit for bit, each field equals
+    # its solo run, and the update counts differ between the fields
+    n, Ln, nu, dt = 4096, 2 * math.pi, 1e-3, 2.5e-4
+    w = S.ns_power_law(n, batch=1)[0]
+    w0 = np.stack([w, 1e-4 * w])
+    kw = dict(lx=Ln, ly=Ln, dt=dt, nu=nu, dealias=1, rfft=1, tol=1e-10)
+    out = []
+    for split in ("1", "0"):
+        monkeypatch.setenv("PSS_COL_SPLIT", split)
+        g = lib.Grid("ns", n, "fp32", batch=2, **kw)
+        g.set_state(w0)
+        g.step(2)
+        g.sync()
+        out.append((g.get_state(), g.stats()[1]))
+        g.close()
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0].view(np.uint32), out[1][0].view(np.uint32))
+    monkeypatch.setenv("PSS_COL_SPLIT", "1")
+    solo_updates = []
+    for f in range(2):
+        g = lib.Grid("ns", n, "fp32", batch=1, **kw)
+        g.set_state(w0[f][None])
+        g.step(2)
+        g.sync()
+        assert np.array_equal(g.get_state()[0].view(np.uint32), out[0][0][f].view(np.uint32))
+        solo_updates.append(g.stats()[1])
+        g.close()
+    assert sum(solo_updates) == out[0][1]
+    assert solo_updates[0] != solo_updates[1]
