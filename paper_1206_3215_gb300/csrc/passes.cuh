@@ -515,6 +515,7 @@ template <class Rl, int N, class Op> struct TmaHalfStore {
     static constexpr size_t SMEM = tma_col_smem<C>() + (ON ? 128 + BYTES : 0);
 };
 
+
 template <class Rl, int N, class Op>
 __global__ void __launch_bounds__(ColCfgOf<Rl, N, Op, 0>::THREADS, ColCfgOf<Rl, N, Op, 0>::MIN_CTAS)
     k_col_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap map_half, Op op,
