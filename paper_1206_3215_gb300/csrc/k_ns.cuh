@@ -234,13 +234,16 @@ template <class Rl, bool MID, bool HALF = false> struct NsCol {
         const Rl kx = __ldg(kxo + xs), kxx = __ldg(kx2 + xs), mx = __ldg(keepx + xs);
         double acc = 0.0;
         float acc_hi = 0.0f, acc_lo = 0.0f;  // FP32: double-float partial of this thread
-        if (live && o0 == 0) {  // the update reads w^n, w^k (and J_hat^n) after the forward transform
+        if (f.active && o0 == 0) {  // the update reads w^n, w^k (and J_hat^n) after the forward transform
+            // by row: thread i of the tile's T W threads asks for rows i, i + T W, ...
+            // (one 32-byte row segment of the tile per request)
+            const int64_t tb = field * N * nx + (x - x % W);
 #pragma unroll
-            for (int m = 0; m < P; ++m) {
-                const int64_t o = int64_t(t + T * m) * nx;
-                prefetch_l2(wn + o);
-                prefetch_l2(wk + o);
-                if (!MID && k > 0) prefetch_l2(jn + base + o);
+            for (int r = t * W + x % W; r < N; r += T * W) {
+                const int64_t o = tb + int64_t(r) * nx;
+                prefetch_l2(wb(f.idx) + o);
+                prefetch_l2(wb(ns_buf(f.idx, k)) + o);
+                if (!MID && k > 0) prefetch_l2(jn + o);
             }
         }
         // pass 0: J_hat and the update; pass p > 0: output p - 1, a derivative
